@@ -1,0 +1,389 @@
+"""CPU oracle for the state-vector Rydberg emulator hot path (complex128, numpy/scipy).
+
+TEST INFRASTRUCTURE ONLY. Nothing in the product path may import this module;
+only tests/, the smoke check and the benchmark's CPU-baseline leg use it. It is
+deliberately plain and slow, and shares no code with the CUDA library.
+
+What it computes (arXiv 2510.09813):
+  * Hilbert space of N two-level atoms, dimension 2**N (Sec. II.A, Eq. (1); the
+    printed C^{2N} is read as (C^2)^{(x)N} = C^{2**N}).
+  * Hamiltonian, Eq. (3), extended with a laser phase phi_i:
+        H = sum_i Omega_i/2 (cos phi_i X_i - sin phi_i Y_i) - sum_i delta_i n_i
+            + sum_{i<j} C6/|r_i - r_j|^6 n_i n_j .
+    With Y = -i|0><1| + i|1><0|, the single-atom drive has <1|h|0> = Omega/2 e^{-i phi}
+    and <0|h|1> = Omega/2 e^{+i phi}.
+  * Basis order: row-major N-index tensor of Eq. (4) (Sec. II.B): atom 0 is the
+    most significant bit, b = sum_i b_i 2^(N-1-i).
+  * Time discretisation, Sec. III and Eq. (5): pulses sampled at t_n = n ns, held
+    constant over each step of dt ns at their midpoint value
+    (s[floor(m)] + s[ceil(m)])/2 with m = (n + 1/2) dt; psi_{k+1} = exp(-i H_k dt) psi_k.
+  * Lanczos (Krylov) evaluation of exp(-i H dt) psi (Sec. III.A), here with full
+    re-orthogonalisation and a tight tolerance so that it reproduces the exact
+    product of exponentials; a dense expm path (N <= 12) is the brute-force check.
+  * Observables <n_i> and bitstring sampling (the emulator results of Sec. III).
+
+Readings of points the paper leaves open are listed where they are used.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import scipy.linalg
+
+# ---------------------------------------------------------------------------
+# Register: pair energies (Eq. (3), third term)
+# ---------------------------------------------------------------------------
+
+
+def pair_interactions(positions, c6: float) -> np.ndarray:
+    """V[i, j] = C6 / |r_i - r_j|^6 for i != j, V[i, i] = 0 (Eq. (3)).
+
+    The paper sums over i > j once per pair; V is returned symmetric so that the
+    pair sum is 0.5 * sum_{i != j}. Coincident atoms are an error.
+    """
+    r = np.asarray(positions, dtype=np.float64)
+    n = r.shape[0]
+    V = np.zeros((n, n))
+    for i in range(n):
+        for j in range(n):
+            if i == j:
+                continue
+            d2 = float(np.sum((r[i] - r[j]) ** 2))
+            if d2 == 0.0:
+                raise ValueError(f"atoms {i} and {j} coincide")
+            V[i, j] = c6 / d2 ** 3
+    return V
+
+
+# ---------------------------------------------------------------------------
+# Time discretisation (Sec. III, Eq. (5))
+# ---------------------------------------------------------------------------
+
+
+def step_schedule(t_ns: int, dt_ns: int):
+    """Steps covering [0, t_ns] ns with step dt_ns.
+
+    Returns a list of (start_ns, length_ns). Reading: when t_ns is not a
+    multiple of dt_ns the last step is shorter (t_ns mod dt_ns) and uses its
+    own midpoint.
+    """
+    if dt_ns < 1 or t_ns < 1:
+        raise ValueError("dt_ns and t_ns must be >= 1")
+    out = []
+    start = 0
+    while start < t_ns:
+        length = min(dt_ns, t_ns - start)
+        out.append((start, length))
+        start += length
+    return out
+
+
+def midpoint_value(samples_row: np.ndarray, start_ns: int, length_ns: int) -> float:
+    """Midpoint rule of Sec. III: m = start + length/2 (= (n + 1/2) dt for a full
+    step); value = (s[floor m] + s[ceil m]) / 2. Indices past the last sample
+    (t_ns - 1) are clamped to it (reading: samples exist for t = 0 .. t_ns-1 ns)."""
+    last = len(samples_row) - 1
+    # m is start + length/2; work in half-nanoseconds to stay in integers.
+    twice_m = 2 * start_ns + length_ns
+    lo = min(twice_m // 2, last)
+    hi = min((twice_m + 1) // 2, last)
+    return 0.5 * (float(samples_row[lo]) + float(samples_row[hi]))
+
+
+def step_parameters(n_atoms: int, t_ns: int, dt_ns: int, omega, delta, phi=None):
+    """Per-step (tau_us, Omega_bar[N], delta_bar[N], phi_bar[N]) by the midpoint rule.
+
+    Pulse arrays are [rows][t_ns] with rows == 1 (global) or rows == n_atoms.
+    """
+    def rows_of(a):
+        a = np.asarray(a, dtype=np.float64)
+        if a.ndim == 1:
+            a = a[None, :]
+        if a.shape[1] != t_ns or a.shape[0] not in (1, n_atoms):
+            raise ValueError("pulse array has the wrong shape")
+        return a
+
+    om = rows_of(omega)
+    de = rows_of(delta)
+    ph = rows_of(phi) if phi is not None else np.zeros((1, t_ns))
+    steps = []
+    for start, length in step_schedule(t_ns, dt_ns):
+        o = np.array([midpoint_value(om[i % om.shape[0]], start, length) for i in range(n_atoms)])
+        d = np.array([midpoint_value(de[i % de.shape[0]], start, length) for i in range(n_atoms)])
+        p = np.array([midpoint_value(ph[i % ph.shape[0]], start, length) for i in range(n_atoms)])
+        steps.append((length / 1000.0, o, d, p))
+    return steps
+
+
+# ---------------------------------------------------------------------------
+# Hamiltonian (Eq. (3)) in the basis of Eq. (4)
+# ---------------------------------------------------------------------------
+
+
+def atom_bit(n_atoms: int, i: int) -> int:
+    """Bit position of atom i: atom 0 is the most significant bit (Eq. (4) row-major)."""
+    return n_atoms - 1 - i
+
+
+def occupation_bits(n_atoms: int, lo: int = 0, hi: int | None = None) -> np.ndarray:
+    """B[b - lo, i] = b_i (occupation of atom i in basis state b), float64."""
+    if hi is None:
+        hi = 2 ** n_atoms
+    b = np.arange(lo, hi, dtype=np.int64)
+    B = np.empty((hi - lo, n_atoms))
+    for i in range(n_atoms):
+        B[:, i] = (b >> atom_bit(n_atoms, i)) & 1
+    return B
+
+
+def diagonal_energies(V: np.ndarray, delta_bar: np.ndarray) -> np.ndarray:
+    """E(b) = sum_{i<j} V_ij b_i b_j - sum_i delta_i b_i (the diagonal of Eq. (3))."""
+    n = V.shape[0]
+    D = 2 ** n
+    E = np.empty(D)
+    chunk = 1 << 18
+    for lo in range(0, D, chunk):
+        hi = min(D, lo + chunk)
+        B = occupation_bits(n, lo, hi)
+        E[lo:hi] = 0.5 * np.einsum("bi,bi->b", B @ V, B) - B @ delta_bar
+    return E
+
+
+def dense_hamiltonian(V, omega_bar, delta_bar, phi_bar) -> np.ndarray:
+    """Dense 2^N x 2^N matrix of Eq. (3), built entry by entry (brute force, N <= 12)."""
+    n = V.shape[0]
+    D = 2 ** n
+    H = np.zeros((D, D), dtype=np.complex128)
+    for b in range(D):
+        occ = [(b >> atom_bit(n, i)) & 1 for i in range(n)]
+        e = 0.0
+        for i in range(n):
+            if occ[i]:
+                e -= delta_bar[i]
+                for j in range(i + 1, n):
+                    if occ[j]:
+                        e += V[i, j]
+        H[b, b] = e
+        for i in range(n):
+            bp = b ^ (1 << atom_bit(n, i))
+            # column b (source), row bp (target)
+            if occ[i] == 0:  # |0> -> |1>: <1|h|0> = Omega/2 e^{-i phi}
+                H[bp, b] += 0.5 * omega_bar[i] * np.exp(-1j * phi_bar[i])
+            else:  # |1> -> |0>: <0|h|1> = Omega/2 e^{+i phi}
+                H[bp, b] += 0.5 * omega_bar[i] * np.exp(1j * phi_bar[i])
+    return H
+
+
+def apply_hamiltonian(psi: np.ndarray, V, omega_bar, delta_bar, phi_bar, E=None) -> np.ndarray:
+    """y = H psi without forming H: the diagonal of Eq. (3) times psi plus, per atom,
+    the drive term acting on the atom's tensor axis (Sec. III.A: 'apply the diagonal,
+    then add the Omega-scaled permutations')."""
+    n = V.shape[0]
+    if E is None:
+        E = diagonal_energies(V, delta_bar)
+    x = np.asarray(psi, dtype=np.complex128)
+    y = E * x
+    yt = y.reshape((2,) * n)
+    xt = x.reshape((2,) * n)
+    for i in range(n):
+        up = 0.5 * omega_bar[i] * np.exp(-1j * phi_bar[i])  # <1|h|0>
+        dn = 0.5 * omega_bar[i] * np.exp(1j * phi_bar[i])  # <0|h|1>
+        sel0 = [slice(None)] * n
+        sel1 = [slice(None)] * n
+        sel0[i] = 0
+        sel1[i] = 1
+        yt[tuple(sel1)] += up * xt[tuple(sel0)]
+        yt[tuple(sel0)] += dn * xt[tuple(sel1)]
+    return y
+
+
+# ---------------------------------------------------------------------------
+# exp(-i H tau) psi
+# ---------------------------------------------------------------------------
+
+
+def tridiagonal(alpha, beta) -> np.ndarray:
+    m = len(alpha)
+    T = np.diag(np.asarray(alpha, dtype=np.float64))
+    for k in range(m - 1):
+        T[k, k + 1] = T[k + 1, k] = beta[k]
+    return T
+
+
+def lanczos_expm(matvec, psi: np.ndarray, tau: float, tol: float = 1e-13, m_max: int = 60):
+    """exp(-i tau H) psi by Lanczos (Sec. III.A), complex128.
+
+    Krylov basis v_0 = psi/|psi|, three-term recurrence for H, then the basis is
+    re-orthogonalised in full (classical Gram-Schmidt, twice) so the oracle does
+    not depend on the recurrence's loss of orthogonality. The small problem
+    exp(-i tau T_m) e_1 is evaluated with scipy's expm. The step is accepted when
+    the a-posteriori estimate beta_m |[exp(-i tau T_m) e_1]_{m-1}| <= tol
+    (relative to |psi|) or on breakdown; otherwise the Krylov space is reused
+    for the largest tau / 2^k that meets tol and the remainder restarts.
+
+    Returns (new_psi, stats) where stats = list of (krylov_dim, tau_taken).
+    """
+    psi = np.array(psi, dtype=np.complex128)
+    remaining = float(tau)
+    stats = []
+    while remaining > 0.0:
+        beta0 = np.linalg.norm(psi)
+        if beta0 == 0.0:
+            return psi, stats
+        V = [psi / beta0]
+        alpha: list[float] = []
+        beta: list[float] = []
+        accepted = None
+        for j in range(m_max):
+            w = matvec(V[j])
+            a = float(np.vdot(V[j], w).real)
+            w = w - a * V[j]
+            if j > 0:
+                w = w - beta[j - 1] * V[j - 1]
+            Vm = np.array(V)
+            for _ in range(2):
+                w = w - Vm.T @ (Vm.conj() @ w)
+            b = float(np.linalg.norm(w))
+            alpha.append(a)
+            T = tridiagonal(alpha, beta)
+            u = scipy.linalg.expm(-1j * remaining * T)[:, 0]
+            scale = max(1.0, float(np.max(np.abs(alpha))) if alpha else 1.0)
+            if b <= 1e-14 * scale or b * abs(u[-1]) <= tol:
+                accepted = (remaining, u)
+                break
+            if j == m_max - 1:
+                t = remaining
+                while True:
+                    t *= 0.5
+                    u = scipy.linalg.expm(-1j * t * T)[:, 0]
+                    if b * abs(u[-1]) <= tol:
+                        break
+                accepted = (t, u)
+                break
+            beta.append(b)
+            V.append(w / b)
+        t, u = accepted
+        m = len(u)
+        psi = beta0 * (np.array(V[:m]).T @ u)
+        stats.append((m, t))
+        remaining -= t
+        if remaining < 1e-15 * tau:
+            remaining = 0.0
+    return psi, stats
+
+
+def zero_state(n_atoms: int) -> np.ndarray:
+    """|0...0> (Sec. II.B.2: the initial state of the QPU)."""
+    psi = np.zeros(2 ** n_atoms, dtype=np.complex128)
+    psi[0] = 1.0
+    return psi
+
+
+def occupations(psi: np.ndarray) -> np.ndarray:
+    """<n_i> = sum_b |psi_b|^2 b_i for every atom i."""
+    n = int(round(math.log2(psi.size)))
+    p = psi.real.astype(np.float64) ** 2 + psi.imag.astype(np.float64) ** 2
+    out = np.zeros(n)
+    pt = p.reshape((2,) * n)
+    for i in range(n):
+        axes = tuple(k for k in range(n) if k != i)
+        out[i] = pt.sum(axis=axes)[1] if n > 1 else pt[1]
+    return out
+
+
+def evolve(positions, c6, t_ns, dt_ns, omega, delta, phi=None, psi0=None,
+           method: str = "krylov", tol: float = 1e-13, m_max: int = 60,
+           record_occupations: bool = True):
+    """psi_K = exp(-i H_{K-1} tau) ... exp(-i H_0 tau) psi_0 (Eq. (5)).
+
+    method = "dense" (expm of the brute-force matrix, N <= 12) or "krylov".
+    Returns (psi_K, occ) where occ[k] = <n_i> after k steps (row 0 = psi_0).
+    """
+    V = pair_interactions(positions, c6)
+    n = V.shape[0]
+    psi = zero_state(n) if psi0 is None else np.array(psi0, dtype=np.complex128)
+    occ = [occupations(psi)] if record_occupations else []
+    for tau, om, de, ph in step_parameters(n, t_ns, dt_ns, omega, delta, phi):
+        if method == "dense":
+            H = dense_hamiltonian(V, om, de, ph)
+            psi = scipy.linalg.expm(-1j * tau * H) @ psi
+        else:
+            E = diagonal_energies(V, de)
+            psi, _ = lanczos_expm(lambda x: apply_hamiltonian(x, V, om, de, ph, E), psi, tau,
+                                  tol=tol, m_max=m_max)
+        if record_occupations:
+            occ.append(occupations(psi))
+    return psi, np.array(occ)
+
+
+# ---------------------------------------------------------------------------
+# Error metrics
+# ---------------------------------------------------------------------------
+
+
+def infidelity(a, b) -> float:
+    """1 - |<a|b>|^2 / (|a|^2 |b|^2), overlap accumulated in complex128."""
+    a = np.asarray(a, dtype=np.complex128)
+    b = np.asarray(b, dtype=np.complex128)
+    ov = np.vdot(a, b)
+    return float(1.0 - abs(ov) ** 2 / (np.vdot(a, a).real * np.vdot(b, b).real))
+
+
+def norm_difference(a, b) -> float:
+    """|a - b| (the metric of Sec. III.A.1, Figs. 3-4)."""
+    return float(np.linalg.norm(np.asarray(a, np.complex128) - np.asarray(b, np.complex128)))
+
+
+# ---------------------------------------------------------------------------
+# Sampling: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) + inverse CDF
+# ---------------------------------------------------------------------------
+
+_M0 = 0xD2511F53
+_M1 = 0xCD9E8D57
+_W0 = 0x9E3779B9
+_W1 = 0xBB67AE85
+_MASK = 0xFFFFFFFF
+
+
+def philox4x32_10(counter, key):
+    """Philox4x32 with 10 rounds, written from its published definition.
+
+    One round maps (c0, c1, c2, c3) with key (k0, k1) to
+    (hi(M1*c2) ^ c1 ^ k0, lo(M1*c2), hi(M0*c0) ^ c3 ^ k1, lo(M0*c0));
+    the key is advanced by the Weyl constants (W0, W1) between rounds.
+    """
+    c = [int(x) & _MASK for x in counter]
+    k0, k1 = int(key[0]) & _MASK, int(key[1]) & _MASK
+    for r in range(10):
+        if r > 0:
+            k0 = (k0 + _W0) & _MASK
+            k1 = (k1 + _W1) & _MASK
+        p0 = _M0 * c[0]
+        p1 = _M1 * c[2]
+        c = [((p1 >> 32) ^ c[1] ^ k0) & _MASK, p1 & _MASK,
+             ((p0 >> 32) ^ c[3] ^ k1) & _MASK, p0 & _MASK]
+    return c
+
+
+def shot_uniform(seed: int, shot: int) -> float:
+    """Uniform in [0, 1) for shot index `shot`: Philox4x32-10 with counter
+    (shot mod 2^32, shot >> 32, 0, 0) and key (seed mod 2^32, seed >> 32);
+    u = ((x0 << 21) | (x1 >> 11)) * 2^-53."""
+    x = philox4x32_10((shot & _MASK, (shot >> 32) & _MASK, 0, 0), (seed & _MASK, (seed >> 32) & _MASK))
+    u53 = (x[0] << 21) | (x[1] >> 11)
+    return u53 * 2.0 ** -53
+
+
+def sample_bitstrings(psi: np.ndarray, shots: int, seed: int) -> np.ndarray:
+    """Basis indices b = min{b : cdf(b) > u * cdf(D-1)} with cdf the running sum of
+    |psi_b|^2 in float64 (|psi_b|^2 = re^2 + im^2)."""
+    p = psi.real.astype(np.float64) ** 2 + psi.imag.astype(np.float64) ** 2
+    cdf = np.cumsum(p)
+    total = cdf[-1]
+    out = np.empty(shots, dtype=np.uint64)
+    for s in range(shots):
+        u = shot_uniform(seed, s)
+        idx = int(np.searchsorted(cdf, u * total, side="right"))
+        out[s] = min(idx, psi.size - 1)
+    return out

@@ -1,0 +1,380 @@
+"""Pins for the CPU oracle against facts that do not come from the oracle itself:
+closed forms, brute force, invariants, symmetries and published test vectors.
+
+Each pin is chosen so that a plausible slip in the oracle (a dropped drive term,
+a wrong sign of delta, a transposed <0|h|1>/<1|h|0>, a reversed bit order, an
+off-by-one midpoint index) fails at least one of them.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg
+
+from oracle import rydberg as O
+from paper_2510_09813_b300 import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------------------
+# Independent closed forms (written here from the physics, not from the oracle)
+# ---------------------------------------------------------------------------
+
+def two_level_propagator(omega, delta, phi, t):
+    """exp(-i h t) for h = [[0, W e^{i phi}], [W e^{-i phi}, -delta]], W = omega/2.
+
+    h = -delta/2 + M with M^2 = w^2 I, w = sqrt(omega^2 + delta^2)/2, so
+    exp(-i h t) = e^{i delta t/2} (cos(w t) I - i sin(w t)/w M).
+    """
+    w = 0.5 * math.hypot(omega, delta)
+    M = np.array([[delta / 2, omega / 2 * np.exp(1j * phi)],
+                  [omega / 2 * np.exp(-1j * phi), -delta / 2]])
+    s = math.sin(w * t) / w if w > 0 else t
+    return np.exp(1j * delta * t / 2) * (math.cos(w * t) * np.eye(2) - 1j * s * M)
+
+
+def kron_all(vs):
+    out = np.array([1.0 + 0j])
+    for v in vs:
+        out = np.kron(out, v)
+    return out
+
+
+# ---------------------------------------------------------------------------
+# Published vectors
+# ---------------------------------------------------------------------------
+
+def test_philox_known_answers():
+    rows = []
+    with open(os.path.join(GOLDEN, "philox4x32_10_kat.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                rows.append([int(x, 16) for x in line.split()])
+    assert len(rows) == 3
+    for r in rows:
+        assert O.philox4x32_10(r[0:4], r[4:6]) == r[6:10]
+
+
+def test_shot_uniform_range_and_mean():
+    u = np.array([O.shot_uniform(1234, s) for s in range(4000)])
+    assert u.min() >= 0.0 and u.max() < 1.0
+    assert abs(u.mean() - 0.5) < 0.02
+    # counters differ -> values differ
+    assert len(np.unique(u)) == u.size
+
+
+# ---------------------------------------------------------------------------
+# Register and Hamiltonian structure
+# ---------------------------------------------------------------------------
+
+def test_pair_interaction_value_and_coincident():
+    V = O.pair_interactions([[0.0, 0.0], [6.0, 0.0], [0.0, 5.0]], 5420158.53)
+    assert V[0, 1] == pytest.approx(5420158.53 / 6.0 ** 6, rel=1e-15)
+    assert V[0, 2] == pytest.approx(5420158.53 / 5.0 ** 6, rel=1e-15)
+    assert V[1, 2] == pytest.approx(5420158.53 / 61.0 ** 3, rel=1e-15)
+    assert np.all(np.diag(V) == 0) and np.allclose(V, V.T)
+    with pytest.raises(ValueError):
+        O.pair_interactions([[1.0, 2.0], [1.0, 2.0]], 1.0)
+
+
+def test_two_atom_diagonal_and_bit_order():
+    # atom 0 is the most significant bit: b = 1 means atom 1 excited.
+    V = O.pair_interactions([[0.0, 0.0], [6.0, 0.0]], 5420158.53)
+    d = np.array([1.5, -0.25])
+    H = O.dense_hamiltonian(V, np.zeros(2), d, np.zeros(2))
+    v01 = 5420158.53 / 46656.0
+    assert np.allclose(np.diag(H).real, [0.0, -d[1], -d[0], v01 - d[0] - d[1]], rtol=0, atol=1e-12)
+    # drive on atom 0 only couples b and b ^ 2
+    H = O.dense_hamiltonian(V, np.array([2.0, 0.0]), np.zeros(2), np.array([0.3, 0.0]))
+    assert H[2, 0] == pytest.approx(1.0 * np.exp(-0.3j))  # <1|h|0> for atom 0
+    assert H[0, 2] == pytest.approx(1.0 * np.exp(0.3j))
+    assert H[1, 0] == 0 and H[3, 1] == pytest.approx(np.exp(-0.3j))
+
+
+def test_dense_is_hermitian_and_matches_matrix_free():
+    rng = np.random.Generator(np.random.PCG64(7))
+    n = 6
+    pos = W.random_register(rng, n, 20.0)
+    V = O.pair_interactions(pos, W.C6_DEFAULT)
+    om, de, ph = rng.uniform(0, 7, n), rng.normal(0, 3, n), rng.uniform(-3, 3, n)
+    H = O.dense_hamiltonian(V, om, de, ph)
+    assert np.allclose(H, H.conj().T, atol=1e-12)
+    x = rng.standard_normal(2 ** n) + 1j * rng.standard_normal(2 ** n)
+    y = O.apply_hamiltonian(x, V, om, de, ph)
+    assert np.allclose(y, H @ x, atol=1e-9)
+    a = rng.standard_normal(2 ** n) + 1j * rng.standard_normal(2 ** n)
+    assert np.vdot(a, O.apply_hamiltonian(x, V, om, de, ph)) == pytest.approx(
+        np.conj(np.vdot(x, O.apply_hamiltonian(a, V, om, de, ph))), rel=1e-12)
+
+
+def test_diagonal_energies_brute_force():
+    rng = np.random.Generator(np.random.PCG64(8))
+    n = 7
+    V = O.pair_interactions(W.random_register(rng, n, 25.0), W.C6_DEFAULT)
+    de = rng.normal(0, 2, n)
+    E = O.diagonal_energies(V, de)
+    for b in [0, 1, 5, 64, 77, 127]:
+        occ = [(b >> (n - 1 - i)) & 1 for i in range(n)]
+        e = sum(V[i, j] for i in range(n) for j in range(n) if i < j and occ[i] and occ[j])
+        e -= sum(de[i] for i in range(n) if occ[i])
+        assert E[b] == pytest.approx(e, rel=1e-13, abs=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# Midpoint rule (Sec. III)
+# ---------------------------------------------------------------------------
+
+def test_step_schedule_and_midpoints():
+    assert O.step_schedule(1000, 10)[:2] == [(0, 10), (10, 10)]
+    assert len(O.step_schedule(1000, 10)) == 100
+    assert O.step_schedule(25, 10) == [(0, 10), (10, 10), (20, 5)]
+    s = np.arange(100, dtype=float) * 3.0 + 1.0  # linear: midpoint value = s(m)
+    # even dt: m integer
+    assert O.midpoint_value(s, 20, 10) == 1.0 + 3.0 * 25
+    # odd dt: m = start + 2.5 -> average of floor and ceil
+    assert O.midpoint_value(s, 10, 5) == 1.0 + 3.0 * 12.5
+    # the last step: indices clamp to the final sample
+    assert O.midpoint_value(s, 99, 1) == 0.5 * (s[99] + s[99])
+    st = O.step_parameters(2, 30, 10, np.vstack([s[:30], 2 * s[:30]]), s[None, :30])
+    assert len(st) == 3 and st[1][0] == pytest.approx(0.01)
+    assert np.allclose(st[1][1], [1 + 3 * 15, 2 * (1 + 3 * 15)])
+
+
+# ---------------------------------------------------------------------------
+# Closed forms of the dynamics
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("method", ["dense", "krylov"])
+def test_single_atom_closed_form_constant_pulse(method):
+    om, de, ph, t_ns = 2 * math.pi * 1.1, 3.7, 0.6, 700
+    psi, occ = O.evolve([[0.0, 0.0]], W.C6_DEFAULT, t_ns, 10, np.full(t_ns, om), np.full(t_ns, de),
+                        np.full(t_ns, ph), method=method)
+    ref = two_level_propagator(om, de, ph, t_ns / 1000.0) @ np.array([1.0, 0.0])
+    assert np.allclose(psi, ref, atol=1e-11)
+    assert occ[-1, 0] == pytest.approx(abs(ref[1]) ** 2, abs=1e-11)
+
+
+def test_full_rabi_cycle():
+    # Omega = 2 pi rad/us, delta = 0: P1(0.5 us) = 1, P1(1 us) = 0.
+    psi, occ = O.evolve([[0.0, 0.0]], 1.0, 1000, 10, np.full(1000, 2 * math.pi), np.zeros(1000))
+    assert occ[50, 0] == pytest.approx(1.0, abs=1e-12)
+    assert occ[100, 0] == pytest.approx(0.0, abs=1e-12)
+
+
+def test_single_atom_piecewise_linear_midpoint():
+    # Linear ramps sampled at 1 ns: the midpoint value of each step is the ramp at
+    # its centre, so the result is a product of exact 2x2 propagators.
+    t_ns, dt = 203, 7  # odd dt and a ragged last step
+    t = np.arange(t_ns) / 1000.0
+    om = 5.0 + 20.0 * t
+    de = -4.0 + 30.0 * t
+    ph = 0.2 + 3.0 * t
+    psi, _ = O.evolve([[0.0, 0.0]], 1.0, t_ns, dt, om, de, ph)
+    ref = np.array([1.0 + 0j, 0.0])
+    start = 0
+    while start < t_ns:
+        length = min(dt, t_ns - start)
+        mid_us = (start + length / 2) / 1000.0
+        mid_us = min(mid_us, (t_ns - 1) / 1000.0)
+        U = two_level_propagator(5.0 + 20.0 * mid_us, -4.0 + 30.0 * mid_us, 0.2 + 3.0 * mid_us,
+                                 length / 1000.0)
+        ref = U @ ref
+        start += length
+    assert np.allclose(psi, ref, atol=1e-11)
+
+
+def test_noninteracting_product_state():
+    # C6 = 0: each atom evolves alone; amplitude b = prod_i c^{(i)}_{b_i} with atom 0 = MSB.
+    n, t_ns = 5, 300
+    om = np.array([1.0, 2.5, 4.0, 5.5, 7.0]) * math.pi
+    de = np.array([-3.0, 0.0, 1.5, 4.0, -6.0])
+    ph = np.array([0.0, 0.4, -1.0, 2.0, 3.0])
+    psi, occ = O.evolve(W.chain(n, 5.0), 0.0, t_ns, 10, np.repeat(om[:, None], t_ns, 1),
+                        np.repeat(de[:, None], t_ns, 1), np.repeat(ph[:, None], t_ns, 1))
+    singles = [two_level_propagator(om[i], de[i], ph[i], t_ns / 1000.0) @ np.array([1.0, 0.0])
+               for i in range(n)]
+    assert np.allclose(psi, kron_all(singles), atol=1e-11)
+    assert np.allclose(occ[-1], [abs(s[1]) ** 2 for s in singles], atol=1e-11)
+
+
+def test_zero_drive_pure_phases():
+    # Omega = 0: psi_b(T) = exp(-i sum_k E_k(b) tau_k) psi_b(0), E from explicit pair loops.
+    rng = np.random.Generator(np.random.PCG64(11))
+    n, t_ns, dt = 6, 95, 10
+    pos = W.random_register(rng, n, 20.0)
+    de_samples = rng.normal(0, 2, (n, t_ns))
+    psi0 = kron_all([v for v in W.random_product_state(12, n)])
+    psi, _ = O.evolve(pos, W.C6_DEFAULT, t_ns, dt, np.zeros((1, t_ns)), de_samples, psi0=psi0)
+    c6 = W.C6_DEFAULT
+    phase = np.zeros(2 ** n)
+    for start, length in O.step_schedule(t_ns, dt):
+        lo = min((2 * start + length) // 2, t_ns - 1)
+        hi = min((2 * start + length + 1) // 2, t_ns - 1)
+        d = 0.5 * (de_samples[:, lo] + de_samples[:, hi])
+        for b in range(2 ** n):
+            occ = [(b >> (n - 1 - i)) & 1 for i in range(n)]
+            e = -sum(d[i] for i in range(n) if occ[i])
+            for i in range(n):
+                for j in range(i + 1, n):
+                    if occ[i] and occ[j]:
+                        e += c6 / np.sum((pos[i] - pos[j]) ** 2) ** 3
+            phase[b] += e * length / 1000.0
+    assert np.allclose(psi, np.exp(-1j * phase) * psi0, atol=1e-10)
+
+
+def test_two_atom_symmetric_subspace():
+    # Equal drive on both atoms: dynamics stays in {|00>, |W>, |11>} with the exact
+    # 3x3 Hamiltonian [[0, O/sqrt2, 0], [O/sqrt2, -d, O/sqrt2], [0, O/sqrt2, V - 2d]].
+    r, om, de, t_ns = 7.0, 2 * math.pi * 1.3, 2.0, 800
+    Vv = W.C6_DEFAULT / r ** 6
+    psi, _ = O.evolve([[0.0, 0.0], [r, 0.0]], W.C6_DEFAULT, t_ns, 10, np.full(t_ns, om), np.full(t_ns, de))
+    h3 = np.array([[0, om / math.sqrt(2), 0], [om / math.sqrt(2), -de, om / math.sqrt(2)],
+                   [0, om / math.sqrt(2), Vv - 2 * de]])
+    ev, U = np.linalg.eigh(h3)
+    c = U @ (np.exp(-1j * ev * t_ns / 1000.0) * (U.T @ np.array([1.0, 0, 0])))
+    assert psi[0] == pytest.approx(c[0], abs=1e-11)
+    assert psi[1] == pytest.approx(c[1] / math.sqrt(2), abs=1e-11)
+    assert psi[2] == pytest.approx(c[1] / math.sqrt(2), abs=1e-11)
+    assert psi[3] == pytest.approx(c[2], abs=1e-11)
+
+
+def test_blockade_limit():
+    # V >> Omega: |11> is blocked, the pair oscillates at sqrt(2) Omega.
+    om, t_ns = 2 * math.pi, 400
+    psi, _ = O.evolve([[0.0, 0.0], [3.0, 0.0]], W.C6_DEFAULT, t_ns, 5, np.full(t_ns, om), np.zeros(t_ns))
+    t = t_ns / 1000.0
+    p_w = abs(psi[1]) ** 2 + abs(psi[2]) ** 2
+    assert p_w == pytest.approx(math.sin(math.sqrt(2) * om * t / 2) ** 2, abs=2e-3)
+    assert abs(psi[3]) ** 2 < 1e-4
+
+
+# ---------------------------------------------------------------------------
+# Brute force agreement and invariants
+# ---------------------------------------------------------------------------
+
+def test_dense_vs_krylov_time_dependent():
+    rng = np.random.Generator(np.random.PCG64(21))
+    prob = W.random_knot_problem(rng, 7, 120, with_phi=True)
+    a, occ_a = O.evolve(prob.positions, prob.c6, prob.t_ns, 10, prob.omega, prob.delta, prob.phi,
+                        method="dense")
+    b, occ_b = O.evolve(prob.positions, prob.c6, prob.t_ns, 10, prob.omega, prob.delta, prob.phi,
+                        method="krylov")
+    assert O.norm_difference(a, b) < 1e-11
+    assert np.max(np.abs(occ_a - occ_b)) < 1e-11
+
+
+def test_krylov_substepping_matches_dense():
+    rng = np.random.Generator(np.random.PCG64(22))
+    prob = W.random_knot_problem(rng, 6, 60)
+    V = O.pair_interactions(prob.positions, prob.c6)
+    tau, om, de, ph = O.step_parameters(6, 60, 60, prob.omega, prob.delta)[0]
+    H = O.dense_hamiltonian(V, om, de, ph)
+    psi0 = W.random_state(3, 6)
+    ref = scipy.linalg.expm(-1j * tau * H) @ psi0
+    E = O.diagonal_energies(V, de)
+    out, stats = O.lanczos_expm(lambda x: O.apply_hamiltonian(x, V, om, de, ph, E), psi0, tau,
+                                tol=1e-13, m_max=5)
+    assert len(stats) > 1  # forced to restart
+    assert O.norm_difference(out, ref) < 1e-11
+
+
+def test_norm_and_energy_conservation_constant_pulse():
+    prob = W.rabi_chain(6, 6.0, t_ns=300)
+    V = O.pair_interactions(prob.positions, prob.c6)
+    n = 6
+    om, de, ph = np.full(n, prob.omega[0, 0]), np.zeros(n), np.zeros(n)
+    psi, _ = O.evolve(prob.positions, prob.c6, prob.t_ns, 10, prob.omega, prob.delta)
+    H = O.dense_hamiltonian(V, om, de, ph)
+    psi0 = O.zero_state(n)
+    assert np.linalg.norm(psi) == pytest.approx(1.0, abs=1e-12)
+    assert np.vdot(psi, H @ psi).real == pytest.approx(np.vdot(psi0, H @ psi0).real, abs=1e-10)
+
+
+def test_time_reversal():
+    # H real (phi = 0): exp(+iH t) = conj(exp(-iH t) conj(.)), so evolving conj(psi_T)
+    # forward and conjugating returns psi_0.
+    rng = np.random.Generator(np.random.PCG64(31))
+    n, t_ns = 6, 200
+    pos = W.random_register(rng, n, 18.0)
+    om, de = np.full(t_ns, 9.0), np.full(t_ns, -2.0)
+    psi0 = W.random_state(5, n)
+    psi_t, _ = O.evolve(pos, W.C6_DEFAULT, t_ns, 10, om, de, psi0=psi0)
+    back, _ = O.evolve(pos, W.C6_DEFAULT, t_ns, 10, om, de, psi0=np.conj(psi_t))
+    assert O.norm_difference(np.conj(back), psi0) < 1e-10
+
+
+def test_mirror_symmetry_rabi_chain():
+    prob = W.rabi_chain(8, 6.0, t_ns=200)
+    _, occ = O.evolve(prob.positions, prob.c6, prob.t_ns, 10, prob.omega, prob.delta)
+    assert np.allclose(occ, occ[:, ::-1], atol=1e-12)
+
+
+def test_uniform_phase_gauge_identity():
+    # H(phi) = U H(0) U^dagger with U = exp(-i phi sum_i n_i): from |0..0>,
+    # amplitude b picks up exp(-i phi popcount(b)).
+    rng = np.random.Generator(np.random.PCG64(41))
+    n, t_ns, phi = 6, 150, 0.9
+    pos = W.random_register(rng, n, 16.0)
+    om, de = np.full(t_ns, 11.0), np.full(t_ns, 1.5)
+    a, _ = O.evolve(pos, W.C6_DEFAULT, t_ns, 10, om, de)
+    b, _ = O.evolve(pos, W.C6_DEFAULT, t_ns, 10, om, de, np.full(t_ns, phi))
+    pop = np.array([bin(k).count("1") for k in range(2 ** n)])
+    assert np.allclose(b, np.exp(-1j * phi * pop) * a, atol=1e-11)
+
+
+def test_atom_permutation_permutes_bits():
+    rng = np.random.Generator(np.random.PCG64(42))
+    n, t_ns = 5, 120
+    pos = W.random_register(rng, n, 15.0)
+    om = rng.uniform(3, 9, n)
+    perm = np.array([3, 0, 4, 1, 2])
+    a, occ_a = O.evolve(pos, W.C6_DEFAULT, t_ns, 10, np.repeat(om[:, None], t_ns, 1), np.zeros((1, t_ns)))
+    b, occ_b = O.evolve(pos[perm], W.C6_DEFAULT, t_ns, 10, np.repeat(om[perm][:, None], t_ns, 1),
+                        np.zeros((1, t_ns)))
+    assert np.allclose(occ_b[-1], occ_a[-1][perm], atol=1e-12)
+    at = a.reshape((2,) * n)
+    assert np.allclose(b.reshape((2,) * n), np.transpose(at, perm), atol=1e-11)
+
+
+# ---------------------------------------------------------------------------
+# Observables, metrics and sampling
+# ---------------------------------------------------------------------------
+
+def test_occupations_and_metrics():
+    singles = W.random_product_state(3, 4)
+    psi = kron_all(singles)
+    assert np.allclose(O.occupations(psi), [abs(s[1]) ** 2 for s in singles], atol=1e-14)
+    assert O.infidelity(psi, 1j * psi) == pytest.approx(0.0, abs=1e-14)
+    x = W.random_state(1, 4)
+    assert O.infidelity(psi, x) == pytest.approx(1 - abs(np.vdot(psi, x)) ** 2, abs=1e-13)
+    assert O.norm_difference(psi, -psi) == pytest.approx(2.0)
+
+
+def test_sampling_distribution():
+    prob = W.rabi_chain(8, 6.0, t_ns=400)
+    psi, _ = O.evolve(prob.positions, prob.c6, prob.t_ns, 10, prob.omega, prob.delta)
+    shots = 20000
+    s = O.sample_bitstrings(psi, shots, seed=99)
+    p = np.abs(psi) ** 2
+    counts = np.bincount(s.astype(np.int64), minlength=256)
+    tv = 0.5 * np.sum(np.abs(counts / shots - p))
+    assert tv < 0.03
+    # inverse CDF by brute force with the same uniforms
+    cdf = np.cumsum(p)
+    for k in range(50):
+        u = O.shot_uniform(99, k) * cdf[-1]
+        b = next(i for i in range(256) if cdf[i] > u)
+        assert s[k] == b
+
+
+def test_paper_memory_figures():
+    # Sec. III.A.1: 16 * 2^N bytes per complex128 vector, ~1 GB at N = 26;
+    # state + diagonal + 15 Krylov vectors below 20 GB.
+    with open(os.path.join(GOLDEN, "paper_memory.txt")) as f:
+        row = [float(x) for x in next(l for l in f if not l.startswith("#")).split()]
+    n, bpa, gb, kv, max_gb = row
+    state = bpa * 2 ** int(n)
+    assert state / 1e9 == pytest.approx(gb, rel=0.1)
+    assert (state * (kv + 1) + 8 * 2 ** int(n)) / 1e9 < max_gb
