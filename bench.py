@@ -1,0 +1,354 @@
+"""Benchmark: Lanczos time steps of the 28-atom random-box workload on B300.
+
+Workload (the metric's "28-atom" configuration): 28 atoms seeded uniformly in a
+30 x 30 um box with minimum spacing 5 um, per-atom Omega_i ~ U(0.8, 1.2) 2 pi
+rad/us and delta_i ~ N(0, pi), constant in time, T = 2 us, dt = 5 ns, complex64
+state (2^28 amplitudes, 2 GiB), Krylov depth <= 20, from |0...0>.
+
+One bench step = one time step of Eq. (5): the full Lanczos evaluation of
+exp(-i H_k dt) psi (both streaming passes per Krylov iteration, the device-side
+tridiagonal exponential and convergence test, Krylov restarts if needed) and the
+combine fused with <n_i>. `value` is time steps per second on the device with the
+state resident; `e2e` runs the same steps through the whole-solve C ABI from host
+inputs (pulses, positions) to host outputs (<n_i> per step).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) each rank runs an independent replica of the workload on
+its own GPU (the path is replicated, not sharded); rank 0 prints the line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_ATOMS = 28
+DT_NS = 5
+M_MAX = 20
+METRIC = "28-atom Lanczos steps/s"
+UNIT = "steps/s"
+WORKLOAD = "random-box N=28 c64 (30x30 um, min spacing 5 um, per-atom Omega~U(0.8,1.2)2pi, delta~N(0,pi)), dt=5 ns, m_max=20"
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("tile_kernels.cu", "rsv_common.cuh", "kernels.h"):
+        h.update(open(os.path.join(ROOT, "paper_2510_09813_b300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kind: str):
+    """DRAM bytes per amplitude of `kind` from the committed ncu summary, if the
+    kernel sources still match the ones that were profiled."""
+    p = os.path.join(ROOT, "profiles", "lanczos_pass_kernels_n28_c64.md")
+    if not os.path.exists(p):
+        return None
+    txt = open(p).read()
+    m = re.search(r"source hash:\s*([0-9a-f]{16})", txt)
+    if not m or m.group(1) != kernel_source_hash():
+        return None
+    m = re.search(rf"traffic_per_amp\[{kind}\]:\s*([0-9.]+)", txt)
+    return float(m.group(1)) if m else None
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the oracle as it stands
+# ---------------------------------------------------------------------------
+
+def oracle_step_sample(n_sample: int = 22):
+    """One oracle Lanczos time step on the first n_sample atoms of the workload
+    (same register, pulses, dt), timed on the host, scaled to N = 28 by the matvec
+    cost ratio 2^(28-n) * 28/n. Returns (steps_per_s_at_28, seconds, cores)."""
+    from oracle import rydberg as O
+    from paper_2510_09813_b300 import workloads as W
+    prob = W.random_box(seed=3, n=N_ATOMS)
+    pos = prob.positions[:n_sample]
+    om = prob.omega[:n_sample, :DT_NS]
+    de = prob.delta[:n_sample, :DT_NS]
+    t0, c0 = time.perf_counter(), time.process_time()
+    O.evolve(pos, prob.c6, DT_NS, DT_NS, om, de, None, method="krylov", tol=1e-7, m_max=M_MAX,
+             record_occupations=True)
+    wall, cpu = time.perf_counter() - t0, time.process_time() - c0
+    scale = 2.0 ** (N_ATOMS - n_sample) * N_ATOMS / n_sample
+    cores = max(1, round(cpu / wall)) if wall > 0 else 1
+    return 1.0 / (wall * scale), wall, cores
+
+
+def reference_arm(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    n_sample = 22
+    for _ in range(args.warmup):
+        oracle_step_sample(n_sample)
+    walls, cores = [], 1
+    for _ in range(args.steps):
+        v, wall, cores = oracle_step_sample(n_sample)
+        walls.append(wall)
+    scale = 2.0 ** (N_ATOMS - n_sample) * N_ATOMS / n_sample
+    per_step = sum(walls) / len(walls) * scale
+    value = 1.0 / per_step
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "c128 (f64)", "data": "synthetic",
+        "config": {"workload": WORKLOAD},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"one oracle Lanczos step (complex128, full re-orthogonalisation, "
+                                   f"tol 1e-7) on the first {n_sample} atoms of the workload per bench step, "
+                                   f"scaled x{scale:.0f} (2^(28-n) * 28/n) to N=28"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# Our arm
+# ---------------------------------------------------------------------------
+
+def ours(args):
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend=backend)
+    torch.cuda.set_device(local)
+    from paper_2510_09813_b300 import api
+    from paper_2510_09813_b300 import workloads as W
+
+    prob = W.random_box(seed=3, n=N_ATOMS)  # T = 2 us -> 400 steps
+    ctx = api.Context(local)
+    stream = torch.cuda.current_stream()
+    solver = api.Solver(ctx, prob, DT_NS, "c64", m_max=M_MAX, obs_stride=1)
+    total_steps = solver.progress()[1]
+    need = args.warmup + args.steps
+    if need > total_steps:
+        raise SystemExit(f"warmup + steps must be <= {total_steps}")
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+
+    solver.step(args.warmup)
+    it0 = solver.stats()["krylov_iterations"]
+    l0 = solver.stats()["kernel_launches"]
+    solver.set_profiling(True)
+    clocks = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    solver.step(args.steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    barrier()
+    ms = ev0.elapsed_time(ev1)
+    if ws > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    kt = solver.kernel_times()
+    solver.set_profiling(False)
+    st = solver.stats()
+    iters = st["krylov_iterations"] - it0
+    launches = st["kernel_launches"] - l0
+    value = ws * args.steps / (ms / 1e3)
+
+    # roofline of the dominant kernel (largest total device time)
+    hbm, src = peaks()
+    dom = max(("pass_first", "pass_second", "combine"), key=lambda k: kt[k]["ms"])
+    amps = 2 ** N_ATOMS
+    per_launch_ms = kt[dom]["ms"] / max(1, kt[dom]["launches"])
+    per_launch_bytes = kt[dom]["bytes"] / max(1, kt[dom]["launches"])
+    achieved = per_launch_bytes / (per_launch_ms / 1e3) / 1e9
+    tr = profiled_traffic(dom)
+    kernels = {}
+    for k in ("pass_first", "pass_second", "combine", "control"):
+        d = kt[k]
+        if d["launches"]:
+            kernels[k] = {"launches": d["launches"], "ms_total": round(d["ms"], 3),
+                          "ms_per_launch": round(d["ms"] / d["launches"], 4),
+                          "algo_GBps": round(d["bytes"] / (d["ms"] / 1e3) / 1e9, 1) if d["ms"] > 0 else None}
+
+    # pure matvec y = H x (two streaming passes, 16 B/amplitude algorithmic)
+    import torch as T
+    x = T.empty(amps, dtype=T.complex64, device="cuda")
+    x.real.normal_()
+    y = T.empty_like(x)
+    V = api.pair_energies(prob.positions, prob.c6)
+    om, de = prob.omega[:, 0], prob.delta[:, 0]
+    for _ in range(3):
+        api.apply_hamiltonian(ctx, N_ATOMS, "c64", V, om, de, None, x, y)
+    torch.cuda.synchronize()
+    reps = 10
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        api.apply_hamiltonian(ctx, N_ATOMS, "c64", V, om, de, None, x, y)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    mv_ms = e0.elapsed_time(e1) / reps
+    mv_gbs = 16 * amps / (mv_ms / 1e3) / 1e9
+    del x, y
+
+    # end to end through the whole-solve ABI: host inputs -> host <n_i> per step
+    e2e_steps = args.steps
+    sub = W.Problem(prob.positions, prob.c6, e2e_steps * DT_NS, prob.omega[:, :e2e_steps * DT_NS],
+                    prob.delta[:, :e2e_steps * DT_NS], None)
+    solver.close()
+    torch.cuda.synchronize()
+    arena = api.footprint_bytes(N_ATOMS, "c64", M_MAX) + (64 << 20)
+    ctx2 = api.Context(local, arena_bytes=arena)
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    res = api.run(ctx2, sub, DT_NS, "c64", m_max=M_MAX, obs_stride=1)
+    occ = res.occupations()
+    e2e_s = time.perf_counter() - t0
+    if ws > 1:
+        t = torch.tensor([e2e_s], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    h2d = (sub.positions.nbytes + sub.omega.nbytes + sub.delta.nbytes) / e2e_steps
+    d2h = occ.nbytes / e2e_steps
+    res.close()
+    ctx2.close()
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        v, wall, cores = oracle_step_sample(22)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"one oracle Lanczos step (complex128, full re-orthogonalisation, tol 1e-7) on the "
+                         f"first 22 atoms of the workload ({wall:.1f} s), scaled x{2.0 ** 6 * 28 / 22:.0f} "
+                         f"(2^(28-22) * 28/22) to N=28"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "c64 (f32 matvec, f64-class reductions)", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_atoms": N_ATOMS, "dt_ns": DT_NS, "m_max": M_MAX,
+                       "parallelism": f"replicas x{ws}",
+                       "l2": "inputs larger than L2 (2 GiB state, 20 x 2 GiB Krylov basis)"},
+            "krylov_iterations_per_step": iters / args.steps,
+            "krylov_iterations_per_s": ws * iters / (ms / 1e3),
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": hbm,
+                         "unit": "GB/s", "frac": round(achieved / hbm, 4),
+                         "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)" if src == "measured" else src,
+                         "traffic": None if tr is None else tr * amps,
+                         "algorithmic_bytes_per_launch": per_launch_bytes},
+            "kernels": kernels,
+            "matvec": {"ms": round(mv_ms, 4), "algo_GBps": round(mv_gbs, 1), "frac_of_peak": round(mv_gbs / hbm, 4),
+                       "algorithmic_bytes": 16 * amps, "passes": 2},
+            "e2e": {"value": e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": round(h2d),
+                    "d2h_bytes_per_step": round(d2h)},
+            "gpu_launches": launches,
+            "clocks": clk,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line))
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    if args.impl == "reference":
+        return reference_arm(args)
+    return ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

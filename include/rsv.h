@@ -1,0 +1,237 @@
+/*
+ * rsv — state-vector emulation of Rydberg atom arrays on NVIDIA B300 (sm_103a).
+ *
+ * C ABI of the time-evolution hot path described in arXiv 2510.09813
+ * ("Efficient Emulation of Neutral Atom Quantum Hardware"), Sec. II-III:
+ *
+ *   H(t) = sum_i Omega_i(t)/2 (cos phi_i X_i - sin phi_i Y_i) - sum_i delta_i(t) n_i
+ *          + sum_{i<j} C6 / |r_i - r_j|^6 n_i n_j                  (Eq. (3), plus a phase)
+ *   psi_{k+1} = exp(-i H_k dt) psi_k                               (Eq. (5))
+ *
+ * with H_k taken at the midpoint of step k from pulses sampled every 1 ns
+ * (Sec. III) and exp(-i H_k dt) psi_k evaluated by Lanczos (Sec. III.A).
+ *
+ * Conventions used by every call:
+ *   - Basis order (Eq. (4), row-major N-index tensor): atom 0 is the most
+ *     significant bit; amplitude index b = sum_i b_i 2^(N-1-i). Sampled
+ *     bitstrings use the same packing.
+ *   - Units: positions in micrometres, Omega and delta in rad/us, phi in rad,
+ *     time in ns (integers) or us (doubles, named *_us), C6 in rad*um^6/us.
+ *   - Precision RSV_C128: complex128 state, FP64 arithmetic. RSV_C64: complex64
+ *     state and FP32 matvec; Krylov inner products/norms are accumulated to
+ *     FP64-class accuracy, the tridiagonal exponential and the pair energies
+ *     are FP64.
+ *   - Amplitude arrays are interleaved (re, im) pairs: 16 bytes per amplitude
+ *     for RSV_C128, 8 bytes for RSV_C64.
+ *   - Errors: every call returns an rsv_status; nothing throws across the ABI.
+ *     rsv_last_error() gives a human-readable message for the calling thread.
+ *   - Streams: all device work of a context is ordered on the context's
+ *     stream (given at creation, or created by the library).
+ */
+#ifndef RSV_H
+#define RSV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define RSV_API __attribute__((visibility("default")))
+#else
+#define RSV_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t rsv_status;
+#define RSV_OK 0
+#define RSV_ERR_INVALID_ARG (-1)      /* bad pointer, size, shape or option */
+#define RSV_ERR_OUT_OF_MEMORY (-2)    /* request exceeds the context's device arena */
+#define RSV_ERR_NOT_CONVERGED (-3)    /* Krylov step needed more than max_substeps restarts */
+#define RSV_ERR_TIMEOUT (-4)          /* a wait ran out (rsv_poll) */
+#define RSV_ERR_CUDA (-5)             /* a CUDA runtime call failed */
+#define RSV_ERR_COINCIDENT_ATOMS (-6) /* two atoms at the same position */
+#define RSV_ERR_NOT_FOUND (-7)        /* unknown ticket */
+
+#define RSV_C128 0
+#define RSV_C64 1
+
+typedef struct rsv_ctx rsv_ctx;
+typedef struct rsv_solver rsv_solver;
+typedef struct rsv_result rsv_result;
+
+/* One emulation problem in the paper's terms (Sec. II.A, Sec. III). All
+ * pointers are host pointers owned by the caller; the library copies what it
+ * needs before the call returns. */
+typedef struct {
+  int32_t n_atoms;             /* 1 .. 30 (RSV_C64) / 1 .. 29 (RSV_C128), bounded by memory */
+  int32_t dim;                 /* 2 or 3: coordinates per atom */
+  const double* positions_um;  /* [n_atoms][dim] */
+  double c6;                   /* interaction constant C of Eq. (3) */
+  int32_t t_ns;                /* number of 1-ns samples = sequence duration in ns */
+  int32_t omega_rows;          /* 1 (same pulse for every atom) or n_atoms */
+  int32_t delta_rows;          /* 1 or n_atoms */
+  int32_t phi_rows;            /* 0 (no phase), 1 or n_atoms */
+  const double* omega;         /* [omega_rows][t_ns], sample n at t = n ns */
+  const double* delta;         /* [delta_rows][t_ns] */
+  const double* phi;           /* [phi_rows][t_ns] or NULL when phi_rows == 0 */
+  const void* initial_state;   /* NULL: |0...0> (the QPU's initial state, Sec. II.B); else
+                                  2^n_atoms amplitudes in the config's precision (host) */
+} rsv_problem;
+
+/* Solver options. Zero fields take the documented default. */
+typedef struct {
+  int32_t dt_ns;        /* step dt, an integer number of ns (Sec. III); required, >= 1 */
+  int32_t precision;    /* RSV_C128 or RSV_C64 */
+  double krylov_tol;    /* precision parameter p of Sec. III.A.1: a Krylov space is accepted
+                           when beta_m |[exp(-i tau T_m) e_1]_{m-1}| <= p. Default 1e-12 (C128),
+                           1e-7 (C64) */
+  int32_t m_max;        /* Krylov dimension cap, 2 .. 64. Default 30. When reached without
+                           convergence the step is split (Krylov restart on a shorter time) */
+  int32_t max_substeps; /* restarts allowed per time step before RSV_ERR_NOT_CONVERGED; default 64 */
+  int32_t obs_stride;   /* record <n_i> every obs_stride steps; 0 records only t = 0 and the end */
+  int32_t reserved;     /* must be 0 */
+} rsv_config;
+
+typedef struct {
+  int64_t steps;              /* time steps taken */
+  int64_t krylov_iterations;  /* matvecs (Lanczos iterations) */
+  int64_t substeps;           /* Krylov restarts beyond one per step */
+  double max_error_estimate;  /* largest accepted a-posteriori Krylov error estimate */
+  double seconds;             /* wall time of the solve on the host */
+  int64_t kernel_launches;    /* library kernels launched so far */
+} rsv_stats;
+
+/* Kernel classes of the time step, for rsv_solver_kernel_times. */
+#define RSV_KERNEL_PASS_FIRST 0  /* contiguous-tile pass: diagonal + low flips (+ the whole matvec if N is small) */
+#define RSV_KERNEL_PASS_SECOND 1 /* strided-tile pass: high flips + Lanczos reductions */
+#define RSV_KERNEL_CONTROL 2     /* Krylov scalar / restart kernels (one block each) */
+#define RSV_KERNEL_COMBINE 3     /* psi = |psi| sum_k u_k v_k fused with <n_i> */
+#define RSV_KERNEL_KINDS 4
+
+typedef struct {
+  double ms[RSV_KERNEL_KINDS];        /* summed device time, CUDA events on the launch stream */
+  int64_t launches[RSV_KERNEL_KINDS];
+  double bytes[RSV_KERNEL_KINDS];     /* summed algorithmic HBM bytes (each operand read or written once) */
+} rsv_kernel_times;
+
+/* ---- context -------------------------------------------------------------- */
+
+/* Creates a context on CUDA device `device`. arena_bytes > 0 caps the device
+ * memory the context may hold (solvers beyond it fail with
+ * RSV_ERR_OUT_OF_MEMORY); 0 means no cap. `cuda_stream` (a cudaStream_t) may
+ * be NULL, in which case the context creates and owns a stream. */
+RSV_API rsv_status rsv_create(rsv_ctx** out, int32_t device, size_t arena_bytes, void* cuda_stream);
+RSV_API void rsv_destroy(rsv_ctx* ctx);
+/* Message of the calling thread's last failed call ("" if none). Valid until
+ * the thread's next rsv_* call. */
+RSV_API const char* rsv_last_error(void);
+/* Library version string. */
+RSV_API const char* rsv_version(void);
+
+/* Device bytes a solve of n_atoms at `precision` with Krylov cap m_max holds:
+ * the state, m_max basis vectors, two work vectors and the tables. This is the
+ * admission footprint; Sec. III.A.1 gives the same accounting for the paper's
+ * complex128 emulator (16 * 2^N bytes per vector). */
+RSV_API size_t rsv_footprint_bytes(int32_t n_atoms, int32_t precision, int32_t m_max);
+
+/* ---- host-side preparation (Sec. II.A, Sec. III) ---------------------------- */
+
+/* Pair energies V[i][j] = C6 / |r_i - r_j|^6 (i != j), V[i][i] = 0, FP64,
+ * written to v_out[n_atoms * n_atoms] (atom order). RSV_ERR_COINCIDENT_ATOMS
+ * if two atoms coincide. */
+RSV_API rsv_status rsv_pair_energies(int32_t n_atoms, int32_t dim, const double* positions_um, double c6, double* v_out);
+
+/* Number of time steps for a sequence of t_ns samples and step dt_ns: the
+ * steps cover [0, t_ns] ns; a last step shorter than dt_ns covers the rest. */
+RSV_API int32_t rsv_num_steps(int32_t t_ns, int32_t dt_ns);
+
+/* Midpoint parameters of every step (Sec. III): for step k starting at s_k with
+ * length l_k (ns), m = s_k + l_k / 2 and the value is (x[floor m] + x[ceil m]) / 2
+ * (sample indices clamped to t_ns - 1). Outputs are [steps][n_atoms] (atom
+ * order) plus tau_us[steps] = l_k / 1000; phi_out may be NULL. */
+RSV_API rsv_status rsv_midpoint_parameters(const rsv_problem* problem, int32_t dt_ns, double* omega_out, double* delta_out,
+                                   double* phi_out, double* tau_us_out);
+
+/* ---- operator-level calls on device buffers ---------------------------------- */
+
+/* y = H x for one constant Hamiltonian of Eq. (3): the fused structured matvec
+ * (diagonal + bit-flip permutations, Sec. III.A). v_pairs is the host
+ * [n_atoms][n_atoms] pair-energy matrix (atom order); omega, delta and phi
+ * (phi may be NULL) are host [n_atoms] arrays. x_dev and y_dev are device
+ * buffers of 2^n_atoms amplitudes in `precision`, caller-owned, 16-byte
+ * aligned, not overlapping. Runs on the context stream; returns after launch. */
+RSV_API rsv_status rsv_apply_hamiltonian(rsv_ctx* ctx, int32_t n_atoms, int32_t precision, const double* v_pairs,
+                                 const double* omega, const double* delta, const double* phi, const void* x_dev,
+                                 void* y_dev);
+
+/* |psi|^2 and <n_i> = sum_b |psi_b|^2 b_i (atom order) of a device state,
+ * accumulated to FP64; results copied to the host arrays (occ may be NULL).
+ * Synchronises the context stream. */
+RSV_API rsv_status rsv_observe(rsv_ctx* ctx, int32_t n_atoms, int32_t precision, const void* psi_dev, double* norm2_out,
+                       double* occ_out);
+
+/* `shots` basis indices drawn from |psi_b|^2 / |psi|^2 of a device state by
+ * inverse CDF (FP64 running sums). Shot s uses Philox4x32-10 with counter
+ * (s mod 2^32, s >> 32, 0, 0) and key (seed mod 2^32, seed >> 32):
+ * u = ((x0 << 21) | (x1 >> 11)) * 2^-53, b = min{b : cdf(b) > u * cdf(D-1)}.
+ * Written to the host array out[shots]. Synchronises the context stream. */
+RSV_API rsv_status rsv_sample(rsv_ctx* ctx, int32_t n_atoms, int32_t precision, const void* psi_dev, int64_t shots,
+                      uint64_t seed, uint64_t* out);
+
+/* ---- solver: a problem resident on the device --------------------------------- */
+
+/* Prepares a problem: pair energies, per-step midpoint parameters, the Krylov
+ * basis and the state (|0...0> or problem->initial_state) on the device. */
+RSV_API rsv_status rsv_solver_create(rsv_ctx* ctx, const rsv_problem* problem, const rsv_config* config, rsv_solver** out);
+RSV_API void rsv_solver_destroy(rsv_solver* s);
+/* Advances up to n_steps time steps (stops at the end of the sequence).
+ * Each step is one Lanczos evaluation of exp(-i H_k dt) psi (Eq. (5)), split
+ * into Krylov restarts when m_max is reached. Records <n_i> per obs_stride.
+ * Returns after the last step's work is complete on the device. */
+RSV_API rsv_status rsv_solver_step(rsv_solver* s, int32_t n_steps);
+/* Steps done so far and steps in the sequence. */
+RSV_API rsv_status rsv_solver_progress(const rsv_solver* s, int32_t* done, int32_t* total);
+/* Borrowed device pointer to the current state (2^n amplitudes), valid until
+ * the solver is destroyed; bytes may be NULL. */
+RSV_API rsv_status rsv_solver_state_device(rsv_solver* s, void** dev_ptr, size_t* bytes);
+/* Copies the current state to host memory (bytes must be the state size). */
+RSV_API rsv_status rsv_solver_get_state(rsv_solver* s, void* host_dst, size_t bytes);
+/* Replaces the current state from host memory (does not reset the step counter). */
+RSV_API rsv_status rsv_solver_set_state(rsv_solver* s, const void* host_src, size_t bytes);
+/* Replaces the current state from a device buffer (copied on the context stream,
+ * after work already queued there). */
+RSV_API rsv_status rsv_solver_set_state_device(rsv_solver* s, const void* dev_src, size_t bytes);
+/* Recorded occupations so far: rows of n_atoms doubles (row 0 = t = 0). If dst
+ * is NULL only *n_rows is set; otherwise up to capacity_rows rows are copied. */
+RSV_API rsv_status rsv_solver_occupations(rsv_solver* s, double* dst, int32_t capacity_rows, int32_t* n_rows);
+RSV_API rsv_status rsv_solver_stats(const rsv_solver* s, rsv_stats* out);
+/* Turns per-launch timing on (1) or off (0). While on, every kernel launch of
+ * rsv_solver_step is bracketed by CUDA events on the context stream and its
+ * duration and algorithmic bytes are accumulated by kernel class; turning it
+ * on also clears the accumulators. Costs two event records per launch. */
+RSV_API rsv_status rsv_solver_set_profiling(rsv_solver* s, int32_t on);
+RSV_API rsv_status rsv_solver_kernel_times(const rsv_solver* s, rsv_kernel_times* out);
+
+/* ---- whole solve ----------------------------------------------------------- */
+
+/* Runs the whole sequence: creates a solver, steps to the end, and returns a
+ * result that owns the final state and the recorded occupations. */
+RSV_API rsv_status rsv_run(rsv_ctx* ctx, const rsv_problem* problem, const rsv_config* config, rsv_result** out);
+/* Final state copied to host memory; bytes = 2^n * (16 or 8). */
+RSV_API rsv_status rsv_result_state(const rsv_result* r, void* host_dst, size_t bytes);
+/* Borrowed device pointer to the final state, valid until rsv_result_free. */
+RSV_API rsv_status rsv_result_state_device(const rsv_result* r, void** dev_ptr, size_t* bytes);
+/* Recorded occupations [rows][n_atoms]; dst NULL queries *n_rows. */
+RSV_API rsv_status rsv_result_occupations(const rsv_result* r, double* dst, int32_t capacity_rows, int32_t* n_rows);
+/* Samples of the final state (see rsv_sample). */
+RSV_API rsv_status rsv_result_sample(const rsv_result* r, int64_t shots, uint64_t seed, uint64_t* out);
+RSV_API rsv_status rsv_result_stats(const rsv_result* r, rsv_stats* out);
+RSV_API void rsv_result_free(rsv_result* r);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RSV_H */

@@ -198,6 +198,35 @@ def apply_hamiltonian(psi: np.ndarray, V, omega_bar, delta_bar, phi_bar, E=None)
     return y
 
 
+def hamiltonian_rows(indices, x, V, omega_bar, delta_bar, phi_bar) -> np.ndarray:
+    """(H x)[b] for each listed b, one row of Eq. (3) at a time: the diagonal
+    element of b plus, per atom, the drive element between b and b with that
+    atom's bit flipped. `x` may be any indexable of complex amplitudes (only the
+    N + 1 entries each row touches are read)."""
+    n = V.shape[0]
+    out = np.empty(len(indices), dtype=np.complex128)
+    for k, b in enumerate(indices):
+        b = int(b)
+        occ = [(b >> atom_bit(n, i)) & 1 for i in range(n)]
+        e = 0.0
+        for i in range(n):
+            if occ[i]:
+                e -= delta_bar[i]
+                for j in range(i + 1, n):
+                    if occ[j]:
+                        e += V[i, j]
+        acc = e * complex(x[b])
+        for i in range(n):
+            bp = b ^ (1 << atom_bit(n, i))
+            if occ[i] == 0:  # row has the atom in |0>: <0|h|1>
+                coef = 0.5 * omega_bar[i] * np.exp(1j * phi_bar[i])
+            else:
+                coef = 0.5 * omega_bar[i] * np.exp(-1j * phi_bar[i])
+            acc += coef * complex(x[bp])
+        out[k] = acc
+    return out
+
+
 # ---------------------------------------------------------------------------
 # exp(-i H tau) psi
 # ---------------------------------------------------------------------------

@@ -1,0 +1,258 @@
+"""Python front end of the rsv C ABI (same names as include/rsv.h, marshalling only).
+
+PyTorch is used for device memory and streams: device buffers are torch CUDA
+tensors (complex64 / complex128) and a Context runs on torch's current CUDA
+stream unless given another one.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _lib as L
+from ._lib import RSV_C64, RSV_C128, RsvError, amp_dtype, check, precision_code  # noqa: F401
+
+
+def _torch():
+    import torch
+    return torch
+
+
+class Context:
+    """rsv_ctx: a device, a stream and a device-memory arena."""
+
+    def __init__(self, device: int = 0, arena_bytes: int = 0, stream=None):
+        torch = _torch()
+        if stream is None:
+            torch.cuda.set_device(device)
+            stream = torch.cuda.current_stream(device).cuda_stream
+        elif hasattr(stream, "cuda_stream"):
+            stream = stream.cuda_stream
+        self.device = device
+        self._h = C.c_void_p()
+        check(L.lib().rsv_create(C.byref(self._h), int(device), int(arena_bytes), C.c_void_p(stream)))
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            L.lib().rsv_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def version() -> str:
+    return L.lib().rsv_version().decode()
+
+
+def footprint_bytes(n_atoms: int, precision="c64", m_max: int = 30) -> int:
+    return int(L.lib().rsv_footprint_bytes(int(n_atoms), precision_code(precision), int(m_max)))
+
+
+def pair_energies(positions, c6: float) -> np.ndarray:
+    pos = np.ascontiguousarray(np.asarray(positions, dtype=np.float64))
+    n, dim = pos.shape
+    out = np.empty((n, n))
+    check(L.lib().rsv_pair_energies(n, dim, L._dptr(pos), float(c6), L._dptr(out)))
+    return out
+
+
+def num_steps(t_ns: int, dt_ns: int) -> int:
+    return int(L.lib().rsv_num_steps(int(t_ns), int(dt_ns)))
+
+
+def midpoint_parameters(problem, dt_ns: int):
+    """(omega[K][n], delta[K][n], phi[K][n], tau_us[K]) by the midpoint rule."""
+    pa = L.ProblemArgs.from_problem(problem)
+    K = num_steps(problem.t_ns, dt_ns)
+    om, de, ph, tau = np.empty((K, pa.n)), np.empty((K, pa.n)), np.empty((K, pa.n)), np.empty(K)
+    check(L.lib().rsv_midpoint_parameters(C.byref(pa.struct), int(dt_ns), L._dptr(om), L._dptr(de),
+                                          L._dptr(ph), L._dptr(tau)))
+    return om, de, ph, tau
+
+
+def _check_state(t, n, precision):
+    torch = _torch()
+    want = torch.complex64 if precision_code(precision) == RSV_C64 else torch.complex128
+    if not (t.is_cuda and t.dtype == want and t.is_contiguous() and t.numel() == 2 ** n):
+        raise ValueError(f"expected a contiguous CUDA {want} tensor of 2**{n} amplitudes")
+    return C.c_void_p(t.data_ptr())
+
+
+def apply_hamiltonian(ctx: Context, n_atoms: int, precision, v_pairs, omega, delta, phi, x, y):
+    """y = H x (Eq. (3)) on CUDA tensors x, y."""
+    V = np.ascontiguousarray(np.asarray(v_pairs, dtype=np.float64))
+    om = np.ascontiguousarray(np.asarray(omega, dtype=np.float64))
+    de = np.ascontiguousarray(np.asarray(delta, dtype=np.float64))
+    ph = None if phi is None else np.ascontiguousarray(np.asarray(phi, dtype=np.float64))
+    check(L.lib().rsv_apply_hamiltonian(
+        ctx.handle, int(n_atoms), precision_code(precision), L._dptr(V), L._dptr(om), L._dptr(de),
+        L._dptr(ph) if ph is not None else C.POINTER(C.c_double)(),
+        _check_state(x, n_atoms, precision), _check_state(y, n_atoms, precision)))
+
+
+def observe(ctx: Context, n_atoms: int, precision, psi):
+    """(|psi|^2, <n_i>[n]) of a CUDA state tensor."""
+    norm2 = C.c_double()
+    occ = np.empty(n_atoms)
+    check(L.lib().rsv_observe(ctx.handle, int(n_atoms), precision_code(precision),
+                              _check_state(psi, n_atoms, precision), C.byref(norm2), L._dptr(occ)))
+    return norm2.value, occ
+
+
+def sample(ctx: Context, n_atoms: int, precision, psi, shots: int, seed: int) -> np.ndarray:
+    out = np.empty(int(shots), dtype=np.uint64)
+    check(L.lib().rsv_sample(ctx.handle, int(n_atoms), precision_code(precision),
+                             _check_state(psi, n_atoms, precision), int(shots), int(seed),
+                             out.ctypes.data_as(C.POINTER(C.c_uint64))))
+    return out
+
+
+class Solver:
+    """rsv_solver: one problem resident on the device, advanced step by step."""
+
+    def __init__(self, ctx: Context, problem, dt_ns: int, precision="c128", krylov_tol=0.0, m_max=0,
+                 max_substeps=0, obs_stride=1, initial_state=None):
+        self.ctx = ctx
+        self.precision = precision_code(precision)
+        init = None
+        if initial_state is not None:
+            init = np.ascontiguousarray(np.asarray(initial_state, dtype=amp_dtype(precision)))
+        self._pa = L.ProblemArgs.from_problem(problem, init)
+        self.n = self._pa.n
+        self._cfg = L.make_config(dt_ns, precision, krylov_tol, m_max, max_substeps, obs_stride)
+        self._h = C.c_void_p()
+        check(L.lib().rsv_solver_create(ctx.handle, C.byref(self._pa.struct), C.byref(self._cfg),
+                                        C.byref(self._h)))
+
+    def step(self, n_steps: int):
+        check(L.lib().rsv_solver_step(self._h, int(n_steps)))
+
+    def progress(self):
+        d, t = C.c_int32(), C.c_int32()
+        check(L.lib().rsv_solver_progress(self._h, C.byref(d), C.byref(t)))
+        return d.value, t.value
+
+    def run_to_end(self):
+        d, t = self.progress()
+        self.step(t - d)
+
+    def state(self) -> np.ndarray:
+        out = np.empty(2 ** self.n, dtype=amp_dtype(self.precision))
+        check(L.lib().rsv_solver_get_state(self._h, C.c_void_p(out.ctypes.data), out.nbytes))
+        return out
+
+    def set_state(self, psi):
+        a = np.ascontiguousarray(np.asarray(psi, dtype=amp_dtype(self.precision)))
+        check(L.lib().rsv_solver_set_state(self._h, C.c_void_p(a.ctypes.data), a.nbytes))
+
+    def set_state_device(self, psi_tensor):
+        """Copy a CUDA tensor (contiguous, the solver's dtype) into the state."""
+        ptr = _check_state(psi_tensor, self.n, self.precision)
+        nbytes = psi_tensor.numel() * psi_tensor.element_size()
+        check(L.lib().rsv_solver_set_state_device(self._h, ptr, nbytes))
+
+    def state_device_ptr(self):
+        p, b = C.c_void_p(), C.c_size_t()
+        check(L.lib().rsv_solver_state_device(self._h, C.byref(p), C.byref(b)))
+        return p.value, b.value
+
+    def occupations(self) -> np.ndarray:
+        rows = C.c_int32()
+        check(L.lib().rsv_solver_occupations(self._h, C.POINTER(C.c_double)(), 0, C.byref(rows)))
+        out = np.empty((rows.value, self.n))
+        check(L.lib().rsv_solver_occupations(self._h, L._dptr(out), rows.value, C.byref(rows)))
+        return out
+
+    def stats(self) -> dict:
+        s = L.Stats_()
+        check(L.lib().rsv_solver_stats(self._h, C.byref(s)))
+        return {k: getattr(s, k) for k, _ in L.Stats_._fields_}
+
+    def set_profiling(self, on: bool):
+        check(L.lib().rsv_solver_set_profiling(self._h, 1 if on else 0))
+
+    def kernel_times(self) -> dict:
+        """{kind: {"ms", "launches", "bytes"}} accumulated while profiling was on."""
+        t = L.KernelTimes_()
+        check(L.lib().rsv_solver_kernel_times(self._h, C.byref(t)))
+        return {k: {"ms": t.ms[i], "launches": t.launches[i], "bytes": t.bytes[i]}
+                for i, k in enumerate(L.KERNEL_KINDS)}
+
+    def close(self):
+        if self._h:
+            L.lib().rsv_solver_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Result:
+    """rsv_result of a whole solve."""
+
+    def __init__(self, h, n, precision):
+        self._h, self.n, self.precision = h, n, precision
+
+    def state(self) -> np.ndarray:
+        out = np.empty(2 ** self.n, dtype=amp_dtype(self.precision))
+        check(L.lib().rsv_result_state(self._h, C.c_void_p(out.ctypes.data), out.nbytes))
+        return out
+
+    def occupations(self) -> np.ndarray:
+        rows = C.c_int32()
+        check(L.lib().rsv_result_occupations(self._h, C.POINTER(C.c_double)(), 0, C.byref(rows)))
+        out = np.empty((rows.value, self.n))
+        check(L.lib().rsv_result_occupations(self._h, L._dptr(out), rows.value, C.byref(rows)))
+        return out
+
+    def sample(self, shots: int, seed: int) -> np.ndarray:
+        out = np.empty(int(shots), dtype=np.uint64)
+        check(L.lib().rsv_result_sample(self._h, int(shots), int(seed), out.ctypes.data_as(C.POINTER(C.c_uint64))))
+        return out
+
+    def stats(self) -> dict:
+        s = L.Stats_()
+        check(L.lib().rsv_result_stats(self._h, C.byref(s)))
+        return {k: getattr(s, k) for k, _ in L.Stats_._fields_}
+
+    def close(self):
+        if self._h:
+            L.lib().rsv_result_free(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def run(ctx: Context, problem, dt_ns: int, precision="c128", krylov_tol=0.0, m_max=0, max_substeps=0,
+        obs_stride=1, initial_state=None) -> Result:
+    """rsv_run: the whole sequence, host inputs in, a Result out."""
+    init = None
+    if initial_state is not None:
+        init = np.ascontiguousarray(np.asarray(initial_state, dtype=amp_dtype(precision)))
+    pa = L.ProblemArgs.from_problem(problem, init)
+    cfg = L.make_config(dt_ns, precision, krylov_tol, m_max, max_substeps, obs_stride)
+    h = C.c_void_p()
+    check(L.lib().rsv_run(ctx.handle, C.byref(pa.struct), C.byref(cfg), C.byref(h)))
+    return Result(h, pa.n, precision_code(precision))

@@ -1,0 +1,82 @@
+// Host-side declarations of the kernel launchers (internal to the library).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "rsv_common.cuh"
+
+namespace rsv {
+
+// Geometry and buffers of one streaming tile pass (see tile_kernels.cu).
+struct TileArgs {
+  int n;         // atoms = state bits
+  int L;         // tile bits
+  int c;         // tile bits [0, c) are amplitude bits [0, c)
+  int a;         // tile bits [c, L) are amplitude bits [a, a + L - c)
+  int f2;        // first amplitude bit of the top fixed range (a + L - c)
+  int nF2;       // bits in the top fixed range (n - f2)
+  int nG;        // lowest nG bits of the top range resolved by partner loads through L2
+  int kt;        // thread bits of the tile layout (<= 8)
+  int64_t num_tiles;
+  const StepParams* sp;  // device
+  const double* vmat;    // device [kMaxAtoms][kMaxAtoms], FP64, by bit position
+  const void* qtab;      // device [2^L] Real, first pass only
+  const void* xin;
+  const void* xprev;
+  void* xout;
+  void* out;
+  const KState* ks;
+  double* partials;      // [grid][3]
+};
+
+enum class TileMode {
+  kMatvecFirst,    // out = E x + flips(tile, G)
+  kMatvecSecond,   // out += flips(tile, G)
+  kLanczosSingle,  // form v_j, matvec, three-term, reductions in one pass
+  kLanczosFirst,   // form v_j, diagonal + low flips - beta v_{j-1}
+  kLanczosSecond,  // + high flips, reductions
+};
+
+cudaError_t launch_tile(const TileArgs& args, TileMode mode, bool c64, bool phi, int grid, cudaStream_t stream);
+
+// Krylov control kernels (krylov_kernels.cu).
+struct ScalarArgs {
+  KState* ks;
+  const double* partials;
+  int nparts;
+  int m_max;
+  int check_from;     // first Krylov dimension at which convergence is tested
+  double tol;         // relative tolerance p of the step
+  double breakdown;   // relative breakdown threshold for beta
+};
+cudaError_t launch_scalar(const ScalarArgs& a, cudaStream_t stream);
+
+struct BeginArgs {
+  KState* ks;
+  const double* partials;  // [nparts][n+1]: |psi|^2 then per-bit sums
+  int nparts;
+  int n;
+  double new_tau;          // > 0: start a new time step of this length
+  double* occ_out;         // nullable: [n] occupations by ATOM index
+  int reset_only;          // 1: only reduce (no Krylov restart)
+};
+cudaError_t launch_begin(const BeginArgs& a, cudaStream_t stream);
+
+struct CombineArgs {
+  int n;
+  int64_t dim;             // 2^n
+  const void* const* basis;  // device array of m_max basis pointers
+  const KState* ks;        // coefficients and m
+  void* psi;               // output (COMBINE) or input (observe only)
+  double* partials;        // [grid][n+1]
+  int combine;
+};
+cudaError_t launch_combine(const CombineArgs& a, bool c64, int grid, cudaStream_t stream);
+
+// Sampling (sample_kernels.cu)
+cudaError_t launch_block_sums(const void* psi, int64_t dim, bool c64, int64_t chunk, double* sums, cudaStream_t stream);
+cudaError_t launch_sample(const void* psi, int64_t dim, bool c64, int64_t chunk, const double* chunk_cdf, int64_t nchunks,
+                          double total, int64_t shots, uint64_t seed, uint64_t* out, cudaStream_t stream);
+
+}  // namespace rsv

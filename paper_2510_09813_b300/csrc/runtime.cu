@@ -1,0 +1,1099 @@
+// Host runtime and C ABI of the B300 state-vector Rydberg library (include/rsv.h).
+//
+//   - device memory arena with an admission cap (footprint accounting as in
+//     arXiv 2510.09813 Sec. III.A.1),
+//   - host preparation: FP64 pair energies (Eq. (3)), midpoint pulse
+//     parameters (Sec. III), bit-position tables for the kernels,
+//   - the Lanczos time-step driver (Sec. III.A, Eq. (5)) over the streaming
+//     tile kernels and the device-side Krylov control kernels.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/rsv.h"
+#include "kernels.h"
+#include "rsv_common.cuh"
+
+using namespace rsv;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+rsv_status fail(rsv_status code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+#define RSV_CUDA(call)                                                                                  \
+  do {                                                                                                  \
+    cudaError_t e_ = (call);                                                                            \
+    if (e_ != cudaSuccess) return fail(RSV_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+#define RSV_TRY(expr)                \
+  do {                               \
+    rsv_status s_ = (expr);          \
+    if (s_ != RSV_OK) return s_;     \
+  } while (0)
+
+constexpr int kTileBitsC64 = 13;
+constexpr int kTileBitsC128 = 12;
+constexpr int kMinSegmentBits = 4;   // contiguous amplitude bits of the strided pass
+constexpr int kMaxSingleGBits = 2;   // bits above the tile resolved in the single pass
+
+int64_t amp_bytes(int precision) { return precision == RSV_C64 ? 8 : 16; }
+
+// ---------------------------------------------------------------------------
+// Device arena: first-fit free list with coalescing over one allocation, or
+// plain cudaMalloc with byte accounting when no cap is given.
+// ---------------------------------------------------------------------------
+class Arena {
+ public:
+  rsv_status init(size_t cap) {
+    cap_ = cap;
+    if (cap_ > 0) {
+      cudaError_t e = cudaMalloc(&base_, cap_);
+      if (e != cudaSuccess) return fail(RSV_ERR_OUT_OF_MEMORY, std::string("arena cudaMalloc: ") + cudaGetErrorString(e));
+      free_[0] = cap_;
+    }
+    return RSV_OK;
+  }
+  ~Arena() {
+    if (base_) cudaFree(base_);
+    for (auto& kv : direct_) cudaFree(kv.first);
+  }
+  rsv_status alloc(size_t bytes, void** out) {
+    std::lock_guard<std::mutex> lk(mu_);
+    bytes = (bytes + 255) & ~size_t(255);
+    if (bytes == 0) bytes = 256;
+    if (cap_ == 0) {
+      void* p = nullptr;
+      cudaError_t e = cudaMalloc(&p, bytes);
+      if (e != cudaSuccess) return fail(RSV_ERR_OUT_OF_MEMORY, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+      direct_[p] = bytes;
+      used_ += bytes;
+      *out = p;
+      return RSV_OK;
+    }
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second >= bytes) {
+        const size_t off = it->first, sz = it->second;
+        free_.erase(it);
+        if (sz > bytes) free_[off + bytes] = sz - bytes;
+        used_map_[off] = bytes;
+        used_ += bytes;
+        *out = static_cast<char*>(base_) + off;
+        return RSV_OK;
+      }
+    }
+    return fail(RSV_ERR_OUT_OF_MEMORY, "arena exhausted: " + std::to_string(bytes) + " bytes requested, " +
+                                           std::to_string(cap_ - used_) + " free (fragmented or full)");
+  }
+  void release(void* p) {
+    if (!p) return;
+    std::lock_guard<std::mutex> lk(mu_);
+    if (cap_ == 0) {
+      auto it = direct_.find(p);
+      if (it != direct_.end()) {
+        used_ -= it->second;
+        cudaFree(p);
+        direct_.erase(it);
+      }
+      return;
+    }
+    const size_t off = static_cast<char*>(p) - static_cast<char*>(base_);
+    auto it = used_map_.find(off);
+    if (it == used_map_.end()) return;
+    size_t sz = it->second;
+    used_ -= sz;
+    used_map_.erase(it);
+    size_t start = off;
+    auto nx = free_.lower_bound(off);
+    if (nx != free_.begin()) {
+      auto pv = std::prev(nx);
+      if (pv->first + pv->second == off) {
+        start = pv->first;
+        sz += pv->second;
+        free_.erase(pv);
+      }
+    }
+    nx = free_.lower_bound(start);
+    if (nx != free_.end() && start + sz == nx->first) {
+      sz += nx->second;
+      free_.erase(nx);
+    }
+    free_[start] = sz;
+  }
+  size_t used() const { return used_; }
+  size_t cap() const { return cap_; }
+
+ private:
+  std::mutex mu_;
+  void* base_ = nullptr;
+  size_t cap_ = 0, used_ = 0;
+  std::map<size_t, size_t> free_;      // offset -> size
+  std::map<size_t, size_t> used_map_;  // offset -> size
+  std::map<void*, size_t> direct_;
+};
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Context
+// ---------------------------------------------------------------------------
+struct rsv_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int num_sms = 0;
+  Arena arena;
+  // scratch for operator-level calls
+  StepParams* d_sp = nullptr;
+  double* d_vmat = nullptr;
+  void* d_qtab = nullptr;
+  KState* d_ks = nullptr;
+  double* d_part = nullptr;  // partial sums (large enough for any grid)
+  double* d_occ = nullptr;
+  KState* h_ks = nullptr;    // pinned
+  std::mutex mu;
+};
+
+namespace {
+
+size_t partials_doubles(int num_sms) { return (size_t)std::max(4 * num_sms, 2048) * (kMaxAtoms + 1); }
+
+struct Plan {
+  TileArgs a{}, b{};   // geometry of the passes
+  bool two_pass = false;
+  int grid_a = 1, grid_b = 1;
+  int grid_c = 1;      // combine/observe grid
+  int L_a = 0;         // tile bits of the first pass (Q table size)
+};
+
+Plan make_plan(int n, bool c64, int num_sms) {
+  Plan p;
+  const int lt = c64 ? kTileBitsC64 : kTileBitsC128;
+  const int v = c64 ? 1 : 0;
+  auto geom = [&](TileArgs& t, int L, int c, int a, int nG) {
+    t.n = n;
+    t.L = L;
+    t.c = c;
+    t.a = a;
+    t.f2 = a + (L - c);
+    t.nF2 = n - t.f2;
+    t.nG = nG;
+    t.kt = std::min(8, L - v);
+    t.num_tiles = int64_t(1) << (n - L);
+  };
+  if (n <= lt) {
+    geom(p.a, n, n, n, 0);
+  } else if (n - lt <= kMaxSingleGBits) {
+    geom(p.a, lt, lt, lt, n - lt);
+  } else {
+    geom(p.a, lt, lt, lt, 0);
+    const int h = std::min(n - lt, lt - kMinSegmentBits);
+    const int c = lt - h;
+    geom(p.b, lt, c, lt, 0);
+    p.b.nG = p.b.nF2;
+    p.two_pass = true;
+  }
+  p.L_a = p.a.L;
+  const int resident = 2 * num_sms;
+  p.grid_a = (int)std::min<int64_t>(p.a.num_tiles, resident);
+  p.grid_b = p.two_pass ? (int)std::min<int64_t>(p.b.num_tiles, resident) : 0;
+  const int T = std::min(n, v + 8 + 4);
+  const int64_t chunks = int64_t(1) << (n - T);
+  p.grid_c = (int)std::min<int64_t>(chunks, 4 * num_sms);
+  return p;
+}
+
+// Q[t] = sum_{q<r<L} V_qr t_q t_r over tile-local bit patterns t (bit positions).
+template <typename Real>
+std::vector<Real> q_table(const std::vector<double>& vbit, int L) {
+  std::vector<double> q(size_t(1) << L, 0.0);
+  for (size_t t = 1; t < q.size(); ++t) {
+    int top = 63 - __builtin_clzll((unsigned long long)t);
+    const size_t rest = t ^ (size_t(1) << top);
+    double s = q[rest];
+    for (int r = 0; r < top; ++r)
+      if ((rest >> r) & 1) s += vbit[top * kMaxAtoms + r];
+    q[t] = s;
+  }
+  return std::vector<Real>(q.begin(), q.end());
+}
+
+// Pair energies by atom (Eq. (3)).
+rsv_status pair_energies(int n, int dim, const double* pos, double c6, std::vector<double>& v) {
+  v.assign((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      if (i == j) continue;
+      double d2 = 0.0;
+      for (int k = 0; k < dim; ++k) {
+        const double d = pos[i * dim + k] - pos[j * dim + k];
+        d2 += d * d;
+      }
+      if (d2 == 0.0)
+        return fail(RSV_ERR_COINCIDENT_ATOMS, "atoms " + std::to_string(i) + " and " + std::to_string(j) + " coincide");
+      v[(size_t)i * n + j] = c6 / (d2 * d2 * d2);
+    }
+  return RSV_OK;
+}
+
+// Atom-ordered [n][n] -> bit-position [kMaxAtoms][kMaxAtoms].
+std::vector<double> to_bit_matrix(int n, const double* v_atoms) {
+  std::vector<double> vb((size_t)kMaxAtoms * kMaxAtoms, 0.0);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) vb[(size_t)(n - 1 - i) * kMaxAtoms + (n - 1 - j)] = v_atoms[(size_t)i * n + j];
+  return vb;
+}
+
+int num_steps(int t_ns, int dt_ns) { return (t_ns + dt_ns - 1) / dt_ns; }
+
+double midpoint(const double* row, int t_ns, int start, int len) {
+  const int twice_m = 2 * start + len;
+  const int lo = std::min(twice_m / 2, t_ns - 1);
+  const int hi = std::min((twice_m + 1) / 2, t_ns - 1);
+  return 0.5 * (row[lo] + row[hi]);
+}
+
+rsv_status validate_problem(const rsv_problem* p) {
+  if (!p) return fail(RSV_ERR_INVALID_ARG, "problem is NULL");
+  if (p->n_atoms < 1 || p->n_atoms > 31) return fail(RSV_ERR_INVALID_ARG, "n_atoms out of range");
+  if (p->dim != 2 && p->dim != 3) return fail(RSV_ERR_INVALID_ARG, "dim must be 2 or 3");
+  if (!p->positions_um) return fail(RSV_ERR_INVALID_ARG, "positions_um is NULL");
+  if (p->t_ns < 1) return fail(RSV_ERR_INVALID_ARG, "t_ns must be >= 1");
+  auto rows_ok = [&](int r, bool allow0) { return r == 1 || r == p->n_atoms || (allow0 && r == 0); };
+  if (!p->omega || !rows_ok(p->omega_rows, false)) return fail(RSV_ERR_INVALID_ARG, "omega rows must be 1 or n_atoms");
+  if (!p->delta || !rows_ok(p->delta_rows, false)) return fail(RSV_ERR_INVALID_ARG, "delta rows must be 1 or n_atoms");
+  if (!rows_ok(p->phi_rows, true) || (p->phi_rows > 0 && !p->phi))
+    return fail(RSV_ERR_INVALID_ARG, "phi rows must be 0, 1 or n_atoms (phi non-NULL when rows > 0)");
+  return RSV_OK;
+}
+
+// Per-step StepParams (bit positions) and step lengths.
+rsv_status step_params(const rsv_problem* p, int dt_ns, std::vector<StepParams>& out) {
+  const int n = p->n_atoms, K = num_steps(p->t_ns, dt_ns);
+  out.assign(K, StepParams{});
+  int start = 0;
+  for (int k = 0; k < K; ++k) {
+    const int len = std::min(dt_ns, p->t_ns - start);
+    StepParams& s = out[k];
+    std::memset(&s, 0, sizeof(s));
+    s.tau = len / 1000.0;
+    s.has_phi = p->phi_rows > 0;
+    for (int i = 0; i < n; ++i) {
+      const int q = n - 1 - i;
+      const double* orow = p->omega + (size_t)(p->omega_rows == 1 ? 0 : i) * p->t_ns;
+      const double* drow = p->delta + (size_t)(p->delta_rows == 1 ? 0 : i) * p->t_ns;
+      s.half_omega[q] = 0.5 * midpoint(orow, p->t_ns, start, len);
+      s.delta[q] = midpoint(drow, p->t_ns, start, len);
+      if (p->phi_rows > 0) {
+        const double* prow = p->phi + (size_t)(p->phi_rows == 1 ? 0 : i) * p->t_ns;
+        s.phi[q] = midpoint(prow, p->t_ns, start, len);
+      }
+    }
+    start += len;
+  }
+  return RSV_OK;
+}
+
+bool any_phi(const std::vector<StepParams>& sp, int n) {
+  for (const auto& s : sp)
+    for (int q = 0; q < n; ++q)
+      if (s.phi[q] != 0.0) return true;
+  return false;
+}
+
+// Launch one streaming pass.
+rsv_status run_pass(rsv_ctx* ctx, TileArgs args, TileMode mode, bool c64, bool phi, int grid) {
+  cudaError_t e = launch_tile(args, mode, c64, phi, grid, ctx->stream);
+  if (e != cudaSuccess) return fail(RSV_ERR_CUDA, std::string("tile kernel launch: ") + cudaGetErrorString(e));
+  return RSV_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Solver
+// ---------------------------------------------------------------------------
+struct rsv_solver {
+  rsv_ctx* ctx = nullptr;
+  int n = 0;
+  int precision = RSV_C128;
+  bool c64 = false;
+  bool phi = false;
+  int64_t dim = 0;
+  rsv_config cfg{};
+  Plan plan;
+  int nsteps = 0, done = 0;
+  std::vector<StepParams> h_sp;
+  // device buffers
+  StepParams* d_sp = nullptr;
+  double* d_vmat = nullptr;
+  void* d_qtab = nullptr;
+  void* d_psi = nullptr;
+  void* d_u[2] = {nullptr, nullptr};
+  std::vector<void*> basis;
+  void** d_basis = nullptr;
+  KState* d_ks = nullptr;
+  double* d_part = nullptr;
+  double* d_cpart = nullptr;
+  double* d_occ = nullptr;   // [max_rows][n]
+  int max_rows = 0, rows = 0;
+  KState* h_ks = nullptr;    // pinned status mirror
+  int last_m = 0;
+  rsv_stats stats{};
+  std::vector<void*> owned;  // arena allocations
+  // live per-launch timing (rsv_solver_set_profiling)
+  bool profiling = false;
+  rsv_kernel_times ktimes{};
+  struct Pending {
+    int kind;
+    double bytes;
+    cudaEvent_t a, b;
+  };
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> event_pool;
+
+  rsv_status alloc(size_t bytes, void** out) {
+    RSV_TRY(ctx->arena.alloc(bytes, out));
+    owned.push_back(*out);
+    return RSV_OK;
+  }
+  ~rsv_solver() {
+    if (ctx) cudaStreamSynchronize(ctx->stream);
+    for (auto& p : pending) {
+      cudaEventDestroy(p.a);
+      cudaEventDestroy(p.b);
+    }
+    for (auto e : event_pool) cudaEventDestroy(e);
+    for (void* p : owned) ctx->arena.release(p);
+    if (h_ks) cudaFreeHost(h_ks);
+  }
+
+  cudaEvent_t take_event() {
+    if (!event_pool.empty()) {
+      cudaEvent_t e = event_pool.back();
+      event_pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+  }
+
+  // Launches through `fn` (returning cudaError_t); with profiling on, brackets
+  // the launch with events on the context stream.
+  template <typename F>
+  rsv_status launch(int kind, double bytes, F&& fn) {
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (profiling) {
+      a = take_event();
+      b = take_event();
+      RSV_CUDA(cudaEventRecord(a, ctx->stream));
+    }
+    cudaError_t e = fn();
+    if (e != cudaSuccess) return fail(RSV_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+    stats.kernel_launches += 1;
+    if (profiling) {
+      RSV_CUDA(cudaEventRecord(b, ctx->stream));
+      pending.push_back({kind, bytes, a, b});
+    }
+    return RSV_OK;
+  }
+
+  // Folds completed launch timings into ktimes (call after a stream sync).
+  void drain_timings() {
+    for (auto& p : pending) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+        ktimes.ms[p.kind] += ms;
+        ktimes.launches[p.kind] += 1;
+        ktimes.bytes[p.kind] += p.bytes;
+      }
+      event_pool.push_back(p.a);
+      event_pool.push_back(p.b);
+    }
+    pending.clear();
+  }
+
+  rsv_status read_status() {
+    RSV_CUDA(cudaMemcpyAsync(h_ks, d_ks, kStatusBytes, cudaMemcpyDeviceToHost, ctx->stream));
+    RSV_CUDA(cudaStreamSynchronize(ctx->stream));
+    if (profiling) drain_timings();
+    return RSV_OK;
+  }
+
+  double vec_bytes() const { return (double)dim * (double)amp_bytes(precision); }
+
+  rsv_status combine(int combine_flag, int m) {
+    CombineArgs ca{};
+    ca.n = n;
+    ca.dim = dim;
+    ca.basis = (const void* const*)d_basis;
+    ca.ks = d_ks;
+    ca.psi = d_psi;
+    ca.partials = d_cpart;
+    ca.combine = combine_flag;
+    const double bytes = combine_flag ? vec_bytes() * (m + 1) : vec_bytes();
+    return launch(RSV_KERNEL_COMBINE, bytes, [&] { return launch_combine(ca, c64, plan.grid_c, ctx->stream); });
+  }
+
+  rsv_status observe_into_partials() { return combine(0, 0); }
+
+  rsv_status begin(double new_tau, int reset_only, double* occ_row) {
+    BeginArgs ba{};
+    ba.ks = d_ks;
+    ba.partials = d_cpart;
+    ba.nparts = plan.grid_c;
+    ba.n = n;
+    ba.new_tau = new_tau;
+    ba.occ_out = occ_row;
+    ba.reset_only = reset_only;
+    return launch(RSV_KERNEL_CONTROL, 0.0, [&] { return launch_begin(ba, ctx->stream); });
+  }
+
+  rsv_status record_row() {
+    if (rows >= max_rows) return RSV_OK;
+    RSV_TRY(begin(0.0, 1, d_occ + (size_t)rows * n));
+    ++rows;
+    return RSV_OK;
+  }
+
+  TileArgs base_args(const TileArgs& g, int step) const {
+    TileArgs a = g;
+    a.sp = d_sp + step;
+    a.vmat = d_vmat;
+    a.qtab = d_qtab;
+    a.ks = d_ks;
+    a.partials = d_part;
+    return a;
+  }
+
+  // Algorithmic bytes: first pass reads u_{j-1} (and v_{j-1} for j > 0) and
+  // writes v_j and its output; the second pass reads v_j and the first pass's
+  // output and writes u_j.
+  rsv_status iteration(int j, int step) {
+    void* u_in = j == 0 ? d_psi : d_u[(j - 1) & 1];
+    void* u_out = d_u[j & 1];
+    TileArgs a = base_args(plan.a, step);
+    a.xin = u_in;
+    a.xprev = j > 0 ? basis[j - 1] : nullptr;
+    a.xout = basis[j];
+    a.out = u_out;
+    const double first_bytes = vec_bytes() * (j > 0 ? 4 : 3);
+    if (!plan.two_pass) {
+      RSV_TRY(launch(RSV_KERNEL_PASS_FIRST, first_bytes,
+                     [&] { return launch_tile(a, TileMode::kLanczosSingle, c64, phi, plan.grid_a, ctx->stream); }));
+    } else {
+      RSV_TRY(launch(RSV_KERNEL_PASS_FIRST, first_bytes,
+                     [&] { return launch_tile(a, TileMode::kLanczosFirst, c64, phi, plan.grid_a, ctx->stream); }));
+      TileArgs b = base_args(plan.b, step);
+      b.xin = basis[j];
+      b.out = u_out;
+      RSV_TRY(launch(RSV_KERNEL_PASS_SECOND, vec_bytes() * 3,
+                     [&] { return launch_tile(b, TileMode::kLanczosSecond, c64, phi, plan.grid_b, ctx->stream); }));
+    }
+    return RSV_OK;
+  }
+
+  rsv_status step_once() {
+    const int k = done;
+    const double tau = h_sp[k].tau;
+    RSV_TRY(begin(tau, 0, nullptr));
+    const int m_max = cfg.m_max;
+    int restarts = 0;
+    while (true) {
+      const int check_from = std::max(1, last_m - 2);
+      ScalarArgs sa{};
+      sa.ks = d_ks;
+      sa.partials = d_part;
+      sa.nparts = plan.two_pass ? plan.grid_b : plan.grid_a;
+      sa.m_max = m_max;
+      sa.check_from = check_from;
+      sa.tol = cfg.krylov_tol;
+      sa.breakdown = 1e-13;
+      int j = 0;
+      bool finished = false;
+      for (; j < m_max; ++j) {
+        RSV_TRY(iteration(j, k));
+        RSV_TRY(launch(RSV_KERNEL_CONTROL, 0.0, [&] { return launch_scalar(sa, ctx->stream); }));
+        if (j + 1 >= check_from) {
+          RSV_TRY(read_status());
+          if (h_ks->status == kIdle) return fail(RSV_ERR_INVALID_ARG, "state has zero norm");
+          if (h_ks->status != kContinue) {
+            finished = true;
+            break;
+          }
+        }
+      }
+      if (!finished) return fail(RSV_ERR_NOT_CONVERGED, "Krylov control did not finish (non-finite values?)");
+      last_m = h_ks->m;
+      stats.krylov_iterations += h_ks->m;
+      stats.max_error_estimate = std::max(stats.max_error_estimate, h_ks->err_est);
+      RSV_TRY(combine(1, h_ks->m));
+      if (h_ks->tau_rem <= 0.0) break;
+      if (++restarts > cfg.max_substeps)
+        return fail(RSV_ERR_NOT_CONVERGED, "step " + std::to_string(k) + " needed more than max_substeps restarts");
+      stats.substeps += 1;
+      RSV_TRY(begin(0.0, 0, nullptr));
+    }
+    ++done;
+    stats.steps += 1;
+    const bool rec = (cfg.obs_stride > 0 && done % cfg.obs_stride == 0) || done == nsteps;
+    if (rec) RSV_TRY(record_row());
+    return RSV_OK;
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Result
+// ---------------------------------------------------------------------------
+struct rsv_result {
+  rsv_solver* solver = nullptr;
+  std::vector<double> occ;
+  int rows = 0;
+};
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char* rsv_last_error(void) { return g_last_error.c_str(); }
+const char* rsv_version(void) { return "rsv 0.1 (sm_103a)"; }
+
+rsv_status rsv_create(rsv_ctx** out, int32_t device, size_t arena_bytes, void* cuda_stream) {
+  g_last_error.clear();
+  if (!out) return fail(RSV_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  int count = 0;
+  RSV_CUDA(cudaGetDeviceCount(&count));
+  if (device < 0 || device >= count) return fail(RSV_ERR_INVALID_ARG, "no such CUDA device");
+  RSV_CUDA(cudaSetDevice(device));
+  rsv_ctx* c = new rsv_ctx();
+  c->device = device;
+  cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+  if (cuda_stream) {
+    c->stream = static_cast<cudaStream_t>(cuda_stream);
+  } else {
+    cudaError_t e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      delete c;
+      return fail(RSV_ERR_CUDA, std::string("cudaStreamCreate: ") + cudaGetErrorString(e));
+    }
+    c->own_stream = true;
+  }
+  rsv_status st = c->arena.init(arena_bytes);
+  auto A = [&](size_t b, void** p) { return st == RSV_OK ? (st = c->arena.alloc(b, p)) : st; };
+  A(sizeof(StepParams), (void**)&c->d_sp);
+  A(sizeof(double) * kMaxAtoms * kMaxAtoms, (void**)&c->d_vmat);
+  A(sizeof(double) << kTileBitsC64, &c->d_qtab);
+  A(sizeof(KState), (void**)&c->d_ks);
+  A(sizeof(double) * partials_doubles(c->num_sms), (void**)&c->d_part);
+  A(sizeof(double) * kMaxAtoms, (void**)&c->d_occ);
+  if (st == RSV_OK) {
+    cudaError_t e = cudaMallocHost(&c->h_ks, sizeof(KState));
+    if (e != cudaSuccess) st = fail(RSV_ERR_CUDA, std::string("cudaMallocHost: ") + cudaGetErrorString(e));
+  }
+  if (st != RSV_OK) {
+    rsv_destroy(c);
+    return st;
+  }
+  *out = c;
+  return RSV_OK;
+}
+
+void rsv_destroy(rsv_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  ctx->arena.release(ctx->d_sp);
+  ctx->arena.release(ctx->d_vmat);
+  ctx->arena.release(ctx->d_qtab);
+  ctx->arena.release(ctx->d_ks);
+  ctx->arena.release(ctx->d_part);
+  ctx->arena.release(ctx->d_occ);
+  if (ctx->h_ks) cudaFreeHost(ctx->h_ks);
+  if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+}
+
+size_t rsv_footprint_bytes(int32_t n_atoms, int32_t precision, int32_t m_max) {
+  if (n_atoms < 1 || n_atoms > 31) return 0;
+  if (m_max <= 0) m_max = 30;
+  const size_t D = size_t(1) << n_atoms;
+  const size_t vec = D * (size_t)amp_bytes(precision);
+  // state + m_max basis vectors + two work vectors + tables/partials
+  return vec * (size_t)(m_max + 3) + (size_t(1) << 20);
+}
+
+rsv_status rsv_pair_energies(int32_t n_atoms, int32_t dim, const double* positions_um, double c6, double* v_out) {
+  g_last_error.clear();
+  if (n_atoms < 1 || (dim != 2 && dim != 3) || !positions_um || !v_out)
+    return fail(RSV_ERR_INVALID_ARG, "bad arguments");
+  std::vector<double> v;
+  RSV_TRY(pair_energies(n_atoms, dim, positions_um, c6, v));
+  std::memcpy(v_out, v.data(), v.size() * sizeof(double));
+  return RSV_OK;
+}
+
+int32_t rsv_num_steps(int32_t t_ns, int32_t dt_ns) {
+  if (t_ns < 1 || dt_ns < 1) return 0;
+  return num_steps(t_ns, dt_ns);
+}
+
+rsv_status rsv_midpoint_parameters(const rsv_problem* problem, int32_t dt_ns, double* omega_out, double* delta_out,
+                                   double* phi_out, double* tau_us_out) {
+  g_last_error.clear();
+  RSV_TRY(validate_problem(problem));
+  if (dt_ns < 1) return fail(RSV_ERR_INVALID_ARG, "dt_ns must be >= 1");
+  std::vector<StepParams> sp;
+  RSV_TRY(step_params(problem, dt_ns, sp));
+  const int n = problem->n_atoms;
+  for (size_t k = 0; k < sp.size(); ++k) {
+    for (int i = 0; i < n; ++i) {
+      const int q = n - 1 - i;
+      if (omega_out) omega_out[k * n + i] = 2.0 * sp[k].half_omega[q];
+      if (delta_out) delta_out[k * n + i] = sp[k].delta[q];
+      if (phi_out) phi_out[k * n + i] = sp[k].phi[q];
+    }
+    if (tau_us_out) tau_us_out[k] = sp[k].tau;
+  }
+  return RSV_OK;
+}
+
+rsv_status rsv_apply_hamiltonian(rsv_ctx* ctx, int32_t n_atoms, int32_t precision, const double* v_pairs,
+                                 const double* omega, const double* delta, const double* phi, const void* x_dev,
+                                 void* y_dev) {
+  g_last_error.clear();
+  if (!ctx || !v_pairs || !omega || !delta || !x_dev || !y_dev) return fail(RSV_ERR_INVALID_ARG, "NULL argument");
+  if (n_atoms < 1 || n_atoms > 31) return fail(RSV_ERR_INVALID_ARG, "n_atoms out of range");
+  if (precision != RSV_C64 && precision != RSV_C128) return fail(RSV_ERR_INVALID_ARG, "bad precision");
+  if ((reinterpret_cast<uintptr_t>(x_dev) | reinterpret_cast<uintptr_t>(y_dev)) & 15)
+    return fail(RSV_ERR_INVALID_ARG, "device buffers must be 16-byte aligned");
+  if (x_dev == y_dev) return fail(RSV_ERR_INVALID_ARG, "x and y must not alias");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  cudaSetDevice(ctx->device);
+  const int n = n_atoms;
+  const bool c64 = precision == RSV_C64;
+  StepParams sp{};
+  std::memset(&sp, 0, sizeof(sp));
+  bool has_phi = false;
+  for (int i = 0; i < n; ++i) {
+    const int q = n - 1 - i;
+    sp.half_omega[q] = 0.5 * omega[i];
+    sp.delta[q] = delta[i];
+    sp.phi[q] = phi ? phi[i] : 0.0;
+    has_phi = has_phi || (phi && phi[i] != 0.0);
+  }
+  sp.has_phi = has_phi;
+  const std::vector<double> vb = to_bit_matrix(n, v_pairs);
+  Plan plan = make_plan(n, c64, ctx->num_sms);
+  RSV_CUDA(cudaMemcpyAsync(ctx->d_sp, &sp, sizeof(sp), cudaMemcpyHostToDevice, ctx->stream));
+  RSV_CUDA(cudaMemcpyAsync(ctx->d_vmat, vb.data(), vb.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  std::vector<float> qf;
+  std::vector<double> qd;
+  if (c64) {
+    qf = q_table<float>(vb, plan.L_a);
+    RSV_CUDA(cudaMemcpyAsync(ctx->d_qtab, qf.data(), qf.size() * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+  } else {
+    qd = q_table<double>(vb, plan.L_a);
+    RSV_CUDA(cudaMemcpyAsync(ctx->d_qtab, qd.data(), qd.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  }
+  TileArgs a = plan.a;
+  a.sp = ctx->d_sp;
+  a.vmat = ctx->d_vmat;
+  a.qtab = ctx->d_qtab;
+  a.ks = ctx->d_ks;
+  a.partials = ctx->d_part;
+  a.xin = x_dev;
+  a.out = y_dev;
+  RSV_TRY(run_pass(ctx, a, TileMode::kMatvecFirst, c64, has_phi, plan.grid_a));
+  if (plan.two_pass) {
+    TileArgs b = plan.b;
+    b.sp = ctx->d_sp;
+    b.vmat = ctx->d_vmat;
+    b.ks = ctx->d_ks;
+    b.partials = ctx->d_part;
+    b.xin = x_dev;
+    b.out = y_dev;
+    RSV_TRY(run_pass(ctx, b, TileMode::kMatvecSecond, c64, has_phi, plan.grid_b));
+  }
+  // keep host staging alive until the copies are done
+  RSV_CUDA(cudaStreamSynchronize(ctx->stream));
+  return RSV_OK;
+}
+
+rsv_status rsv_observe(rsv_ctx* ctx, int32_t n_atoms, int32_t precision, const void* psi_dev, double* norm2_out,
+                       double* occ_out) {
+  g_last_error.clear();
+  if (!ctx || !psi_dev) return fail(RSV_ERR_INVALID_ARG, "NULL argument");
+  if (n_atoms < 1 || n_atoms > 31) return fail(RSV_ERR_INVALID_ARG, "n_atoms out of range");
+  if (precision != RSV_C64 && precision != RSV_C128) return fail(RSV_ERR_INVALID_ARG, "bad precision");
+  if (reinterpret_cast<uintptr_t>(psi_dev) & 15) return fail(RSV_ERR_INVALID_ARG, "psi must be 16-byte aligned");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  cudaSetDevice(ctx->device);
+  const bool c64 = precision == RSV_C64;
+  Plan plan = make_plan(n_atoms, c64, ctx->num_sms);
+  CombineArgs ca{};
+  ca.n = n_atoms;
+  ca.dim = int64_t(1) << n_atoms;
+  ca.ks = ctx->d_ks;
+  ca.psi = const_cast<void*>(psi_dev);
+  ca.partials = ctx->d_part;
+  ca.combine = 0;
+  RSV_CUDA(launch_combine(ca, c64, plan.grid_c, ctx->stream));
+  BeginArgs ba{};
+  ba.ks = ctx->d_ks;
+  ba.partials = ctx->d_part;
+  ba.nparts = plan.grid_c;
+  ba.n = n_atoms;
+  ba.occ_out = ctx->d_occ;
+  ba.reset_only = 1;
+  RSV_CUDA(launch_begin(ba, ctx->stream));
+  RSV_CUDA(cudaMemcpyAsync(ctx->h_ks, ctx->d_ks, kStatusBytes, cudaMemcpyDeviceToHost, ctx->stream));
+  std::vector<double> occ(n_atoms);
+  RSV_CUDA(cudaMemcpyAsync(occ.data(), ctx->d_occ, sizeof(double) * n_atoms, cudaMemcpyDeviceToHost, ctx->stream));
+  RSV_CUDA(cudaStreamSynchronize(ctx->stream));
+  if (norm2_out) *norm2_out = ctx->h_ks->norm2;
+  if (occ_out) std::memcpy(occ_out, occ.data(), sizeof(double) * n_atoms);
+  return RSV_OK;
+}
+
+rsv_status rsv_sample(rsv_ctx* ctx, int32_t n_atoms, int32_t precision, const void* psi_dev, int64_t shots,
+                      uint64_t seed, uint64_t* out) {
+  g_last_error.clear();
+  if (!ctx || !psi_dev || (!out && shots > 0)) return fail(RSV_ERR_INVALID_ARG, "NULL argument");
+  if (n_atoms < 1 || n_atoms > 31 || shots < 0) return fail(RSV_ERR_INVALID_ARG, "bad size");
+  if (precision != RSV_C64 && precision != RSV_C128) return fail(RSV_ERR_INVALID_ARG, "bad precision");
+  if (shots == 0) return RSV_OK;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  cudaSetDevice(ctx->device);
+  const bool c64 = precision == RSV_C64;
+  const int64_t dim = int64_t(1) << n_atoms;
+  const int64_t chunk = std::min<int64_t>(dim, 4096);
+  const int64_t nchunks = (dim + chunk - 1) / chunk;
+  double* d_sums = nullptr;
+  uint64_t* d_out = nullptr;
+  RSV_TRY(ctx->arena.alloc(sizeof(double) * nchunks, (void**)&d_sums));
+  rsv_status st = ctx->arena.alloc(sizeof(uint64_t) * shots, (void**)&d_out);
+  if (st != RSV_OK) {
+    ctx->arena.release(d_sums);
+    return st;
+  }
+  auto cleanup = [&]() {
+    cudaStreamSynchronize(ctx->stream);
+    ctx->arena.release(d_sums);
+    ctx->arena.release(d_out);
+  };
+  std::vector<double> sums(nchunks), cdf(nchunks);
+  cudaError_t e = launch_block_sums(psi_dev, dim, c64, chunk, d_sums, ctx->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(sums.data(), d_sums, sizeof(double) * nchunks, cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) {
+    cleanup();
+    return fail(RSV_ERR_CUDA, std::string("sampling sums: ") + cudaGetErrorString(e));
+  }
+  double run = 0.0;
+  for (int64_t c = 0; c < nchunks; ++c) {
+    cdf[c] = run;
+    run += sums[c];
+  }
+  const double total = run;
+  if (!(total > 0.0)) {
+    cleanup();
+    return fail(RSV_ERR_INVALID_ARG, "state has zero norm");
+  }
+  e = cudaMemcpyAsync(d_sums, cdf.data(), sizeof(double) * nchunks, cudaMemcpyHostToDevice, ctx->stream);
+  if (e == cudaSuccess) e = launch_sample(psi_dev, dim, c64, chunk, d_sums, nchunks, total, shots, seed, d_out, ctx->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out, d_out, sizeof(uint64_t) * shots, cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  cleanup();
+  if (e != cudaSuccess) return fail(RSV_ERR_CUDA, std::string("sampling: ") + cudaGetErrorString(e));
+  return RSV_OK;
+}
+
+rsv_status rsv_solver_create(rsv_ctx* ctx, const rsv_problem* problem, const rsv_config* config, rsv_solver** out) {
+  g_last_error.clear();
+  if (!ctx || !config || !out) return fail(RSV_ERR_INVALID_ARG, "NULL argument");
+  *out = nullptr;
+  RSV_TRY(validate_problem(problem));
+  rsv_config cfg = *config;
+  if (cfg.dt_ns < 1) return fail(RSV_ERR_INVALID_ARG, "dt_ns must be >= 1");
+  if (cfg.precision != RSV_C64 && cfg.precision != RSV_C128) return fail(RSV_ERR_INVALID_ARG, "bad precision");
+  if (cfg.m_max == 0) cfg.m_max = 30;
+  if (cfg.m_max < 2 || cfg.m_max > kMaxKrylov) return fail(RSV_ERR_INVALID_ARG, "m_max must be in [2, 64]");
+  if (cfg.krylov_tol <= 0.0) cfg.krylov_tol = cfg.precision == RSV_C64 ? 1e-7 : 1e-12;
+  if (cfg.max_substeps <= 0) cfg.max_substeps = 64;
+  if (cfg.obs_stride < 0) return fail(RSV_ERR_INVALID_ARG, "obs_stride must be >= 0");
+  const int n = problem->n_atoms;
+  if (cfg.precision == RSV_C128 && n > 30) return fail(RSV_ERR_INVALID_ARG, "n_atoms too large for complex128");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  cudaSetDevice(ctx->device);
+  if (ctx->arena.cap() > 0 &&
+      rsv_footprint_bytes(n, cfg.precision, cfg.m_max) > ctx->arena.cap() - ctx->arena.used())
+    return fail(RSV_ERR_OUT_OF_MEMORY, "footprint exceeds the free arena");
+  std::vector<double> v_atoms;
+  RSV_TRY(pair_energies(n, problem->dim, problem->positions_um, problem->c6, v_atoms));
+  auto s = new rsv_solver();
+  s->ctx = ctx;
+  s->n = n;
+  s->precision = cfg.precision;
+  s->c64 = cfg.precision == RSV_C64;
+  s->dim = int64_t(1) << n;
+  s->cfg = cfg;
+  s->plan = make_plan(n, s->c64, ctx->num_sms);
+  RSV_TRY(step_params(problem, cfg.dt_ns, s->h_sp));
+  s->nsteps = (int)s->h_sp.size();
+  s->phi = any_phi(s->h_sp, n);
+  const std::vector<double> vb = to_bit_matrix(n, v_atoms.data());
+  const size_t vbytes = (size_t)s->dim * amp_bytes(cfg.precision);
+  s->max_rows = (cfg.obs_stride > 0 ? s->nsteps / cfg.obs_stride : 0) + 2;
+  rsv_status st = RSV_OK;
+  auto A = [&](size_t b, void** p) {
+    if (st == RSV_OK) st = s->alloc(b, p);
+  };
+  A(sizeof(StepParams) * s->nsteps, (void**)&s->d_sp);
+  A(sizeof(double) * kMaxAtoms * kMaxAtoms, (void**)&s->d_vmat);
+  A(amp_bytes(cfg.precision) / 2 * (size_t(1) << s->plan.L_a), &s->d_qtab);
+  A(vbytes, &s->d_psi);
+  A(vbytes, &s->d_u[0]);
+  A(vbytes, &s->d_u[1]);
+  s->basis.assign(cfg.m_max, nullptr);
+  for (int k = 0; k < cfg.m_max; ++k) A(vbytes, &s->basis[k]);
+  A(sizeof(void*) * cfg.m_max, (void**)&s->d_basis);
+  A(sizeof(KState), (void**)&s->d_ks);
+  A(sizeof(double) * partials_doubles(ctx->num_sms), (void**)&s->d_part);
+  A(sizeof(double) * partials_doubles(ctx->num_sms), (void**)&s->d_cpart);
+  A(sizeof(double) * n * s->max_rows, (void**)&s->d_occ);
+  if (st != RSV_OK) {
+    delete s;
+    return st;
+  }
+  cudaError_t e = cudaMallocHost(&s->h_ks, sizeof(KState));
+  if (e != cudaSuccess) {
+    delete s;
+    return fail(RSV_ERR_CUDA, std::string("cudaMallocHost: ") + cudaGetErrorString(e));
+  }
+  auto fin = [&](rsv_status r) {
+    if (r != RSV_OK) delete s;
+    return r;
+  };
+  std::vector<char> zero_ks(sizeof(KState), 0);
+  if (cudaMemcpyAsync(s->d_sp, s->h_sp.data(), sizeof(StepParams) * s->nsteps, cudaMemcpyHostToDevice, ctx->stream) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(s->d_vmat, vb.data(), vb.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(s->d_basis, s->basis.data(), sizeof(void*) * cfg.m_max, cudaMemcpyHostToDevice, ctx->stream) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(s->d_ks, zero_ks.data(), sizeof(KState), cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess)
+    return fin(fail(RSV_ERR_CUDA, "upload failed"));
+  if (s->c64) {
+    auto q = q_table<float>(vb, s->plan.L_a);
+    if (cudaMemcpyAsync(s->d_qtab, q.data(), q.size() * sizeof(float), cudaMemcpyHostToDevice, ctx->stream) !=
+        cudaSuccess)
+      return fin(fail(RSV_ERR_CUDA, "upload failed"));
+    cudaStreamSynchronize(ctx->stream);
+  } else {
+    auto q = q_table<double>(vb, s->plan.L_a);
+    if (cudaMemcpyAsync(s->d_qtab, q.data(), q.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream) !=
+        cudaSuccess)
+      return fin(fail(RSV_ERR_CUDA, "upload failed"));
+    cudaStreamSynchronize(ctx->stream);
+  }
+  // initial state
+  if (problem->initial_state) {
+    if (cudaMemcpyAsync(s->d_psi, problem->initial_state, vbytes, cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess)
+      return fin(fail(RSV_ERR_CUDA, "initial state upload failed"));
+  } else {
+    if (cudaMemsetAsync(s->d_psi, 0, vbytes, ctx->stream) != cudaSuccess)
+      return fin(fail(RSV_ERR_CUDA, "memset failed"));
+    if (s->c64) {
+      const float one[2] = {1.f, 0.f};
+      if (cudaMemcpyAsync(s->d_psi, one, sizeof(one), cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess)
+        return fin(fail(RSV_ERR_CUDA, "upload failed"));
+    } else {
+      const double one[2] = {1.0, 0.0};
+      if (cudaMemcpyAsync(s->d_psi, one, sizeof(one), cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess)
+        return fin(fail(RSV_ERR_CUDA, "upload failed"));
+    }
+  }
+  if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return fin(fail(RSV_ERR_CUDA, "sync failed"));
+  rsv_status r = s->observe_into_partials();
+  if (r == RSV_OK) r = s->record_row();
+  if (r == RSV_OK && cudaStreamSynchronize(ctx->stream) != cudaSuccess) r = fail(RSV_ERR_CUDA, "sync failed");
+  if (r != RSV_OK) return fin(r);
+  *out = s;
+  return RSV_OK;
+}
+
+void rsv_solver_destroy(rsv_solver* s) { delete s; }
+
+rsv_status rsv_solver_step(rsv_solver* s, int32_t n_steps) {
+  g_last_error.clear();
+  if (!s || n_steps < 0) return fail(RSV_ERR_INVALID_ARG, "bad arguments");
+  std::lock_guard<std::mutex> lk(s->ctx->mu);
+  cudaSetDevice(s->ctx->device);
+  const auto t0 = std::chrono::steady_clock::now();
+  for (int i = 0; i < n_steps && s->done < s->nsteps; ++i) RSV_TRY(s->step_once());
+  RSV_CUDA(cudaStreamSynchronize(s->ctx->stream));
+  if (s->profiling) s->drain_timings();
+  s->stats.seconds += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  return RSV_OK;
+}
+
+rsv_status rsv_solver_progress(const rsv_solver* s, int32_t* done, int32_t* total) {
+  if (!s) return fail(RSV_ERR_INVALID_ARG, "NULL solver");
+  if (done) *done = s->done;
+  if (total) *total = s->nsteps;
+  return RSV_OK;
+}
+
+rsv_status rsv_solver_state_device(rsv_solver* s, void** dev_ptr, size_t* bytes) {
+  if (!s || !dev_ptr) return fail(RSV_ERR_INVALID_ARG, "NULL argument");
+  *dev_ptr = s->d_psi;
+  if (bytes) *bytes = (size_t)s->dim * amp_bytes(s->precision);
+  return RSV_OK;
+}
+
+rsv_status rsv_solver_get_state(rsv_solver* s, void* host_dst, size_t bytes) {
+  g_last_error.clear();
+  if (!s || !host_dst) return fail(RSV_ERR_INVALID_ARG, "NULL argument");
+  if (bytes != (size_t)s->dim * amp_bytes(s->precision)) return fail(RSV_ERR_INVALID_ARG, "size mismatch");
+  std::lock_guard<std::mutex> lk(s->ctx->mu);
+  RSV_CUDA(cudaMemcpyAsync(host_dst, s->d_psi, bytes, cudaMemcpyDeviceToHost, s->ctx->stream));
+  RSV_CUDA(cudaStreamSynchronize(s->ctx->stream));
+  return RSV_OK;
+}
+
+rsv_status rsv_solver_set_state(rsv_solver* s, const void* host_src, size_t bytes) {
+  g_last_error.clear();
+  if (!s || !host_src) return fail(RSV_ERR_INVALID_ARG, "NULL argument");
+  if (bytes != (size_t)s->dim * amp_bytes(s->precision)) return fail(RSV_ERR_INVALID_ARG, "size mismatch");
+  std::lock_guard<std::mutex> lk(s->ctx->mu);
+  RSV_CUDA(cudaMemcpyAsync(s->d_psi, host_src, bytes, cudaMemcpyHostToDevice, s->ctx->stream));
+  RSV_TRY(s->observe_into_partials());
+  RSV_CUDA(cudaStreamSynchronize(s->ctx->stream));
+  return RSV_OK;
+}
+
+rsv_status rsv_solver_set_state_device(rsv_solver* s, const void* dev_src, size_t bytes) {
+  g_last_error.clear();
+  if (!s || !dev_src) return fail(RSV_ERR_INVALID_ARG, "NULL argument");
+  if (bytes != (size_t)s->dim * amp_bytes(s->precision)) return fail(RSV_ERR_INVALID_ARG, "size mismatch");
+  std::lock_guard<std::mutex> lk(s->ctx->mu);
+  RSV_CUDA(cudaMemcpyAsync(s->d_psi, dev_src, bytes, cudaMemcpyDeviceToDevice, s->ctx->stream));
+  RSV_TRY(s->observe_into_partials());
+  RSV_CUDA(cudaStreamSynchronize(s->ctx->stream));
+  return RSV_OK;
+}
+
+rsv_status rsv_solver_occupations(rsv_solver* s, double* dst, int32_t capacity_rows, int32_t* n_rows) {
+  g_last_error.clear();
+  if (!s || !n_rows) return fail(RSV_ERR_INVALID_ARG, "NULL argument");
+  *n_rows = s->rows;
+  if (!dst) return RSV_OK;
+  const int rows = std::min(capacity_rows, s->rows);
+  std::lock_guard<std::mutex> lk(s->ctx->mu);
+  RSV_CUDA(cudaMemcpyAsync(dst, s->d_occ, sizeof(double) * s->n * rows, cudaMemcpyDeviceToHost, s->ctx->stream));
+  RSV_CUDA(cudaStreamSynchronize(s->ctx->stream));
+  return RSV_OK;
+}
+
+rsv_status rsv_solver_set_profiling(rsv_solver* s, int32_t on) {
+  g_last_error.clear();
+  if (!s) return fail(RSV_ERR_INVALID_ARG, "NULL solver");
+  std::lock_guard<std::mutex> lk(s->ctx->mu);
+  RSV_CUDA(cudaStreamSynchronize(s->ctx->stream));
+  s->drain_timings();
+  s->profiling = on != 0;
+  if (s->profiling) s->ktimes = rsv_kernel_times{};
+  return RSV_OK;
+}
+
+rsv_status rsv_solver_kernel_times(const rsv_solver* s, rsv_kernel_times* out) {
+  if (!s || !out) return fail(RSV_ERR_INVALID_ARG, "NULL argument");
+  *out = s->ktimes;
+  return RSV_OK;
+}
+
+rsv_status rsv_solver_stats(const rsv_solver* s, rsv_stats* out) {
+  if (!s || !out) return fail(RSV_ERR_INVALID_ARG, "NULL argument");
+  *out = s->stats;
+  return RSV_OK;
+}
+
+rsv_status rsv_run(rsv_ctx* ctx, const rsv_problem* problem, const rsv_config* config, rsv_result** out) {
+  g_last_error.clear();
+  if (!out) return fail(RSV_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  rsv_solver* s = nullptr;
+  RSV_TRY(rsv_solver_create(ctx, problem, config, &s));
+  rsv_status st = rsv_solver_step(s, s->nsteps);
+  if (st != RSV_OK) {
+    rsv_solver_destroy(s);
+    return st;
+  }
+  auto r = new rsv_result();
+  r->solver = s;
+  r->rows = s->rows;
+  r->occ.resize((size_t)s->rows * s->n);
+  int32_t rows = 0;
+  st = rsv_solver_occupations(s, r->occ.data(), s->rows, &rows);
+  if (st != RSV_OK) {
+    rsv_result_free(r);
+    return st;
+  }
+  *out = r;
+  return RSV_OK;
+}
+
+rsv_status rsv_result_state(const rsv_result* r, void* host_dst, size_t bytes) {
+  if (!r) return fail(RSV_ERR_INVALID_ARG, "NULL result");
+  return rsv_solver_get_state(r->solver, host_dst, bytes);
+}
+
+rsv_status rsv_result_state_device(const rsv_result* r, void** dev_ptr, size_t* bytes) {
+  if (!r) return fail(RSV_ERR_INVALID_ARG, "NULL result");
+  return rsv_solver_state_device(r->solver, dev_ptr, bytes);
+}
+
+rsv_status rsv_result_occupations(const rsv_result* r, double* dst, int32_t capacity_rows, int32_t* n_rows) {
+  if (!r || !n_rows) return fail(RSV_ERR_INVALID_ARG, "NULL argument");
+  *n_rows = r->rows;
+  if (dst) {
+    const int rows = std::min(capacity_rows, r->rows);
+    std::memcpy(dst, r->occ.data(), sizeof(double) * rows * r->solver->n);
+  }
+  return RSV_OK;
+}
+
+rsv_status rsv_result_sample(const rsv_result* r, int64_t shots, uint64_t seed, uint64_t* out) {
+  if (!r) return fail(RSV_ERR_INVALID_ARG, "NULL result");
+  return rsv_sample(r->solver->ctx, r->solver->n, r->solver->precision, r->solver->d_psi, shots, seed, out);
+}
+
+rsv_status rsv_result_stats(const rsv_result* r, rsv_stats* out) {
+  if (!r) return fail(RSV_ERR_INVALID_ARG, "NULL result");
+  return rsv_solver_stats(r->solver, out);
+}
+
+void rsv_result_free(rsv_result* r) {
+  if (!r) return;
+  rsv_solver_destroy(r->solver);
+  delete r;
+}
+
+}  // extern "C"

@@ -1,0 +1,112 @@
+// Bitstring sampling from |psi_b|^2 (the measurement results an emulator returns,
+// arXiv 2510.09813 Sec. III): b = min{ b : cdf(b) > u * cdf(D-1) }, with the
+// running sum of |psi_b|^2 = re^2 + im^2 in FP64 and uniforms u from
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), one counter per shot.
+//
+// The state is cut into chunks; chunk sums are sequential FP64 sums (one thread
+// per chunk, in index order), their exclusive prefix is formed on the host, and
+// each shot binary-searches the chunk prefix then scans its chunk in order.
+#include "kernels.h"
+#include "rsv_common.cuh"
+
+namespace rsv {
+
+template <typename Real>
+__device__ __forceinline__ double prob_at(const void* psi, int64_t b) {
+  using C = typename CplxT<Real>::type;
+  const C v = reinterpret_cast<const C*>(psi)[b];
+  const double re = (double)v.x, im = (double)v.y;
+  return re * re + im * im;
+}
+
+template <typename Real>
+__global__ void chunk_sum_kernel(const void* psi, int64_t dim, int64_t chunk, double* sums) {
+  const int64_t nchunks = (dim + chunk - 1) / chunk;
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nchunks) return;
+  const int64_t lo = c * chunk, hi = lo + chunk < dim ? lo + chunk : dim;
+  double s = 0.0;
+  for (int64_t b = lo; b < hi; ++b) s += prob_at<Real>(psi, b);
+  sums[c] = s;
+}
+
+__device__ __forceinline__ void philox_round(uint32_t (&x)[4], uint32_t k0, uint32_t k1) {
+  const uint32_t m0 = 0xD2511F53u, m1 = 0xCD9E8D57u;
+  const uint32_t hi0 = __umulhi(m0, x[0]), lo0 = m0 * x[0];
+  const uint32_t hi1 = __umulhi(m1, x[2]), lo1 = m1 * x[2];
+  const uint32_t y0 = hi1 ^ x[1] ^ k0, y1 = lo1, y2 = hi0 ^ x[3] ^ k1, y3 = lo0;
+  x[0] = y0;
+  x[1] = y1;
+  x[2] = y2;
+  x[3] = y3;
+}
+
+__device__ __forceinline__ double shot_uniform(uint64_t seed, uint64_t shot) {
+  uint32_t x[4] = {(uint32_t)shot, (uint32_t)(shot >> 32), 0u, 0u};
+  uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    philox_round(x, k0, k1);
+  }
+  const uint64_t u53 = ((uint64_t)x[0] << 21) | (uint64_t)(x[1] >> 11);
+  return (double)u53 * 0x1.0p-53;
+}
+
+template <typename Real>
+__global__ void sample_kernel(const void* psi, int64_t dim, int64_t chunk, const double* chunk_cdf, int64_t nchunks,
+                              double total, int64_t shots, uint64_t seed, uint64_t* out) {
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= shots) return;
+  const double target = shot_uniform(seed, (uint64_t)s) * total;
+  // last chunk whose exclusive prefix is <= target
+  int64_t lo = 0, hi = nchunks - 1;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi + 1) >> 1;
+    if (chunk_cdf[mid] <= target) lo = mid;
+    else hi = mid - 1;
+  }
+  double run = chunk_cdf[lo];
+  const int64_t b0 = lo * chunk, b1 = b0 + chunk < dim ? b0 + chunk : dim;
+  int64_t pick = -1, last_nonzero = -1;
+  for (int64_t b = b0; b < b1; ++b) {
+    const double p = prob_at<Real>(psi, b);
+    run += p;
+    if (p > 0.0) last_nonzero = b;
+    if (run > target) {
+      pick = b;
+      break;
+    }
+  }
+  if (pick < 0) pick = last_nonzero >= 0 ? last_nonzero : (b1 - 1);
+  out[s] = (uint64_t)pick;
+}
+
+cudaError_t launch_block_sums(const void* psi, int64_t dim, bool c64, int64_t chunk, double* sums, cudaStream_t stream) {
+  const int64_t nchunks = (dim + chunk - 1) / chunk;
+  const int threads = 128;
+  const int64_t blocks = (nchunks + threads - 1) / threads;
+  if (c64)
+    chunk_sum_kernel<float><<<(unsigned)blocks, threads, 0, stream>>>(psi, dim, chunk, sums);
+  else
+    chunk_sum_kernel<double><<<(unsigned)blocks, threads, 0, stream>>>(psi, dim, chunk, sums);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sample(const void* psi, int64_t dim, bool c64, int64_t chunk, const double* chunk_cdf, int64_t nchunks,
+                          double total, int64_t shots, uint64_t seed, uint64_t* out, cudaStream_t stream) {
+  const int threads = 128;
+  const int64_t blocks = (shots + threads - 1) / threads;
+  if (blocks == 0) return cudaSuccess;
+  if (c64)
+    sample_kernel<float><<<(unsigned)blocks, threads, 0, stream>>>(psi, dim, chunk, chunk_cdf, nchunks, total, shots,
+                                                                    seed, out);
+  else
+    sample_kernel<double><<<(unsigned)blocks, threads, 0, stream>>>(psi, dim, chunk, chunk_cdf, nchunks, total, shots,
+                                                                     seed, out);
+  return cudaGetLastError();
+}
+
+}  // namespace rsv

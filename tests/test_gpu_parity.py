@@ -1,0 +1,391 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Tolerances (complex128 path / complex64 path):
+  * matvec: max |y_gpu - y_ref| <= tol * (|E|_max + sum_i |Omega_i|/2) * max|x|
+    with tol = 1e-13 / 2e-6 (FP64 vs FP32 rounding of a sum of N+1 terms);
+  * time evolution: infidelity <= 1e-10 / 1e-5 against the oracle, plus a raw
+    norm difference <= 1e-9 for complex128 (no global phase is dropped);
+  * occupations: max |d<n_i>| <= 1e-10 / 1e-5.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import rydberg as O
+from paper_2510_09813_b300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+MATVEC_TOL = {"c128": 1e-13, "c64": 2e-6}
+INFID_TOL = {"c128": 1e-10, "c64": 1e-5}
+OCC_TOL = {"c128": 1e-10, "c64": 1e-5}
+TDT = {"c128": torch.complex128, "c64": torch.complex64}
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA GPU required for -m gpu tests")
+    from paper_2510_09813_b300 import api
+    c = api.Context(0)
+    yield c
+    c.close()
+
+
+def api():
+    from paper_2510_09813_b300 import api as A
+    return A
+
+
+def rand_state_gpu(n, prec, seed):
+    g = torch.Generator(device="cuda")
+    g.manual_seed(seed)
+    dt = torch.float32 if prec == "c64" else torch.float64
+    re = torch.randn(2 ** n, generator=g, device="cuda", dtype=dt)
+    im = torch.randn(2 ** n, generator=g, device="cuda", dtype=dt)
+    v = torch.complex(re, im)
+    return v / torch.linalg.vector_norm(v)
+
+
+def scale_of(V, om, de):
+    n = V.shape[0]
+    return float(np.sum(np.abs(V)) / 2 + np.sum(np.abs(de)) + np.sum(np.abs(om)) / 2 + 1.0)
+
+
+# ---------------------------------------------------------------------------
+# Matvec y = H x
+# ---------------------------------------------------------------------------
+
+MATVEC_CASES = [(n, p) for p in ("c128", "c64") for n in (1, 2, 3, 5, 8, 9, 11, 12, 13, 14, 15, 16, 18, 20, 22)]
+MATVEC_CASES += [(24, "c64"), (23, "c128")]
+
+
+@pytest.mark.parametrize("n,prec", MATVEC_CASES)
+@pytest.mark.parametrize("with_phi", [False, True])
+def test_matvec_matches_oracle(ctx, n, prec, with_phi):
+    if n >= 20 and with_phi:
+        pytest.skip("phase variant covered at smaller sizes")
+    rng = np.random.Generator(np.random.PCG64(1000 + n))
+    side = 5.0 * math.ceil(math.sqrt(n)) + 5.0
+    pos = W.random_register(rng, n, side)
+    V = O.pair_interactions(pos, W.C6_DEFAULT)
+    om = rng.uniform(2.0, 9.0, n)
+    de = rng.normal(0.0, 3.0, n)
+    ph = rng.uniform(-math.pi, math.pi, n) if with_phi else np.zeros(n)
+    x = rand_state_gpu(n, prec, seed=n)
+    y = torch.empty_like(x)
+    api().apply_hamiltonian(ctx, n, prec, V, om, de, ph if with_phi else None, x, y)
+    torch.cuda.synchronize()
+    xh = x.cpu().numpy().astype(np.complex128)
+    ref = O.apply_hamiltonian(xh, V, om, de, ph)
+    err = np.max(np.abs(y.cpu().numpy().astype(np.complex128) - ref))
+    assert err <= MATVEC_TOL[prec] * scale_of(V, om, de) * np.max(np.abs(xh)), err
+
+
+@pytest.mark.parametrize("prec", ["c64", "c128"])
+def test_matvec_full_size_sampled_rows(ctx, prec):
+    """N = 28 random box (c64) / N = 26 (c128): rows of H x checked one by one."""
+    n = 28 if prec == "c64" else 26
+    prob = W.random_box(seed=3, n=n)
+    V = O.pair_interactions(prob.positions, prob.c6)
+    om, de = prob.omega[:, 0], prob.delta[:, 0]
+    x = rand_state_gpu(n, prec, seed=99)
+    y = torch.empty_like(x)
+    api().apply_hamiltonian(ctx, n, prec, V, om, de, None, x, y)
+    torch.cuda.synchronize()
+    rng = np.random.Generator(np.random.PCG64(5))
+    D = 2 ** n
+    idx = [0, 1, D - 1, D - 2, 2 ** 13 - 1, 2 ** 13, 2 ** 22, 2 ** 22 - 1] + list(rng.integers(0, D, 120))
+    need = sorted({int(b) for b in idx} | {int(b) ^ (1 << q) for b in idx for q in range(n)})
+    xs = x[torch.tensor(need, device="cuda")].cpu().numpy().astype(np.complex128)
+    lookup = dict(zip(need, xs))
+    ref = O.hamiltonian_rows(idx, lookup, V, om, de, np.zeros(n))
+    got = y[torch.tensor(idx, device="cuda")].cpu().numpy().astype(np.complex128)
+    err = np.max(np.abs(got - ref))
+    assert err <= MATVEC_TOL[prec] * scale_of(V, om, de) * np.max(np.abs(xs)), err
+
+
+# ---------------------------------------------------------------------------
+# Time evolution against the oracle
+# ---------------------------------------------------------------------------
+
+def gpu_evolve(ctx, prob, dt, prec, **kw):
+    s = api().Solver(ctx, prob, dt, prec, **kw)
+    s.run_to_end()
+    return s.state().astype(np.complex128), s.occupations(), s.stats()
+
+
+def oracle_evolve(prob, dt, psi0=None):
+    return O.evolve(prob.positions, prob.c6, prob.t_ns, dt, prob.omega, prob.delta, prob.phi, psi0=psi0,
+                    method="krylov", tol=1e-14)
+
+
+@pytest.fixture(scope="module")
+def rabi_chain_ref():
+    prob = W.rabi_chain()  # 8 atoms, 6 um, Omega = 2 pi, T = 1 us
+    psi, occ = oracle_evolve(prob, 10)
+    return prob, psi, occ
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+def test_rabi_chain_n8(ctx, rabi_chain_ref, prec):
+    prob, ref, occ_ref = rabi_chain_ref
+    psi, occ, st = gpu_evolve(ctx, prob, 10, prec)
+    assert st["steps"] == 100
+    assert occ.shape == occ_ref.shape
+    assert O.infidelity(psi, ref) <= INFID_TOL[prec]
+    if prec == "c128":
+        assert O.norm_difference(psi, ref) <= 1e-9
+    assert np.max(np.abs(occ - occ_ref)) <= OCC_TOL[prec]
+
+
+@pytest.fixture(scope="module")
+def sweep_3x4_ref():
+    prob = W.adiabatic_sweep_lattice(3, 4)
+    psi, occ = oracle_evolve(prob, 10)
+    return prob, psi, occ
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+def test_adiabatic_sweep_3x4_full_length(ctx, sweep_3x4_ref, prec):
+    prob, ref, occ_ref = sweep_3x4_ref
+    psi, occ, st = gpu_evolve(ctx, prob, 10, prec)
+    assert st["steps"] == 400
+    assert O.infidelity(psi, ref) <= INFID_TOL[prec]
+    if prec == "c128":
+        assert O.norm_difference(psi, ref) <= 1e-9
+    assert np.max(np.abs(occ - occ_ref)) <= OCC_TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+def test_adiabatic_sweep_4x5_window(ctx, prec):
+    """The 20-atom 4x5 lattice, three steps from t = 2 us of the sweep (peak drive,
+    delta crossing zero), from a random state: full-size geometry of both passes."""
+    full = W.adiabatic_sweep_lattice(4, 5)
+    lo, hi = 2000, 2020
+    prob = W.Problem(full.positions, full.c6, hi - lo, full.omega[:, lo:hi], full.delta[:, lo:hi], None)
+    psi0 = W.random_state(20, 20)
+    ref, occ_ref = oracle_evolve(prob, 10, psi0=psi0)
+    psi, occ, _ = gpu_evolve(ctx, prob, 10, prec, initial_state=psi0)
+    assert O.infidelity(psi, ref) <= INFID_TOL[prec]
+    if prec == "c128":
+        assert O.norm_difference(psi, ref) <= 1e-9
+    assert np.max(np.abs(occ - occ_ref)) <= OCC_TOL[prec]
+
+
+@pytest.mark.parametrize("n,prec", [(1, "c128"), (1, "c64"), (2, "c64"), (6, "c128"), (10, "c64"), (14, "c128"),
+                                    (15, "c64"), (16, "c64"), (17, "c128")])
+def test_random_problems_with_phase(ctx, n, prec):
+    """Time-dependent global pulses with a phase, odd dt and a ragged last step."""
+    rng = np.random.Generator(np.random.PCG64(300 + n))
+    prob = W.random_knot_problem(rng, n, 47, with_phi=True)
+    psi0 = W.random_state(n, n)
+    ref, occ_ref = oracle_evolve(prob, 7, psi0=psi0)
+    psi, occ, _ = gpu_evolve(ctx, prob, 7, prec, initial_state=psi0)
+    assert O.infidelity(psi, ref) <= INFID_TOL[prec]
+    assert np.max(np.abs(occ - occ_ref)) <= OCC_TOL[prec]
+
+
+def test_per_atom_pulses(ctx):
+    rng = np.random.Generator(np.random.PCG64(17))
+    n, t_ns = 9, 60
+    pos = W.random_register(rng, n, 20.0)
+    prob = W.Problem(pos, W.C6_DEFAULT, t_ns, rng.uniform(2, 12, (n, t_ns)), rng.normal(0, 4, (n, t_ns)),
+                     rng.uniform(-1, 1, (n, t_ns)))
+    ref, occ_ref = oracle_evolve(prob, 5)
+    for prec in ("c128", "c64"):
+        psi, occ, _ = gpu_evolve(ctx, prob, 5, prec)
+        assert O.infidelity(psi, ref) <= INFID_TOL[prec]
+        assert np.max(np.abs(occ - occ_ref)) <= OCC_TOL[prec]
+
+
+def test_krylov_restarts_match(ctx):
+    """m_max small forces restarts inside a step; the result must not change."""
+    prob = W.rabi_chain(8, 5.0, omega=4 * math.pi, t_ns=100)
+    ref, _ = oracle_evolve(prob, 50)
+    psi, _, st = gpu_evolve(ctx, prob, 50, "c128", m_max=4)
+    assert st["substeps"] > 0
+    assert O.infidelity(psi, ref) <= 1e-10
+
+
+def test_zero_drive_diagonal(ctx):
+    """Omega = 0 from a superposition: H is diagonal but the Krylov space still grows."""
+    n, t_ns = 10, 50
+    rng = np.random.Generator(np.random.PCG64(4))
+    prob = W.Problem(W.random_register(rng, n, 20.0), W.C6_DEFAULT, t_ns, np.zeros(t_ns),
+                     rng.normal(0, 3, t_ns), None)
+    psi0 = W.random_state(8, n)
+    ref, _ = oracle_evolve(prob, 10, psi0=psi0)
+    psi, _, st = gpu_evolve(ctx, prob, 10, "c128", initial_state=psi0)
+    assert O.infidelity(psi, ref) <= 1e-10
+    assert O.norm_difference(psi, ref) <= 1e-9
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+def test_zero_drive_breakdown(ctx, prec):
+    """Omega = 0 from |0...0>: H psi = 0, the Krylov space breaks down at m = 1
+    and the state must stay exactly |0...0>."""
+    n, t_ns = 12, 30
+    prob = W.Problem(W.chain(n, 5.0), W.C6_DEFAULT, t_ns, np.zeros(t_ns), np.full(t_ns, 2.0), None)
+    psi, occ, st = gpu_evolve(ctx, prob, 10, prec)
+    assert st["krylov_iterations"] == 3
+    assert psi[0] == 1.0 and np.all(psi[1:] == 0)
+
+
+# ---------------------------------------------------------------------------
+# Full-size (N = 28, complex64) closed forms
+# ---------------------------------------------------------------------------
+
+def test_n28_noninteracting_product_state(ctx):
+    """C6 = 0 on the 28-atom random box: each atom is an independent Rabi problem."""
+    base = W.random_box(seed=3, n=28, t_ns=40)
+    prob = W.Problem(base.positions, 0.0, base.t_ns, base.omega, base.delta, None)
+    s = api().Solver(ctx, prob, 5, "c64", obs_stride=8)
+    s.run_to_end()
+    occ = s.occupations()
+    t = base.t_ns / 1000.0
+    singles = []
+    for i in range(28):
+        om, de = base.omega[i, 0], base.delta[i, 0]
+        w = 0.5 * math.hypot(om, de)
+        c0 = np.exp(1j * de * t / 2) * (math.cos(w * t) - 1j * de / 2 * math.sin(w * t) / w)
+        c1 = np.exp(1j * de * t / 2) * (-1j * om / 2 * math.sin(w * t) / w)
+        singles.append((c0, c1))
+    assert np.max(np.abs(occ[-1] - [abs(c[1]) ** 2 for c in singles])) <= 1e-5
+    ptr, nbytes = s.state_device_ptr()
+    rng = np.random.Generator(np.random.PCG64(1))
+    idx = [0, 2 ** 28 - 1] + list(rng.integers(0, 2 ** 28, 64))
+    psi = s.state()
+    for b in idx:
+        amp = 1.0 + 0j
+        for i in range(28):
+            amp *= singles[i][(int(b) >> (27 - i)) & 1]
+        assert abs(complex(psi[int(b)]) - amp) <= 1e-5 * max(1.0, abs(amp)) + 1e-6
+
+
+def test_n28_zero_drive_phases(ctx):
+    """Omega = 0 on the 28-atom random box from a random product state:
+    psi_b(T) = exp(-i T E(b)) psi_b(0) with E from explicit pair sums."""
+    base = W.random_box(seed=3, n=28, t_ns=10)
+    n = 28
+    prob = W.Problem(base.positions, base.c6, base.t_ns, np.zeros((1, base.t_ns)), base.delta, None)
+    singles = W.random_product_state(5, n)
+    # build the product state on the GPU (input construction)
+    psi0 = torch.ones(1, dtype=torch.complex64, device="cuda")
+    for i in range(n):
+        psi0 = torch.kron(psi0, torch.tensor(singles[i], dtype=torch.complex64, device="cuda"))
+    s = api().Solver(ctx, prob, 2, "c64", obs_stride=0, m_max=40)
+    s.set_state_device(psi0)
+    s.run_to_end()
+    psi = s.state()
+    V = O.pair_interactions(base.positions, base.c6)
+    de = base.delta[:, 0]
+    T = base.t_ns / 1000.0
+    rng = np.random.Generator(np.random.PCG64(2))
+    for b in [0, 2 ** 28 - 1] + list(rng.integers(0, 2 ** 28, 48)):
+        b = int(b)
+        occ = [(b >> (n - 1 - i)) & 1 for i in range(n)]
+        e = -sum(de[i] for i in range(n) if occ[i])
+        e += sum(V[i, j] for i in range(n) for j in range(i + 1, n) if occ[i] and occ[j])
+        a0 = 1.0 + 0j
+        for i in range(n):
+            a0 *= singles[i][occ[i]]
+        ref = np.exp(-1j * e * T) * a0
+        assert abs(complex(psi[b]) - ref) <= 3e-4 * abs(a0) + 1e-9
+
+
+def test_n28_norm_conservation_random_box(ctx):
+    prob = W.random_box(seed=3, n=28, t_ns=20)
+    s = api().Solver(ctx, prob, 5, "c64", m_max=20, obs_stride=1)
+    s.run_to_end()
+    ptr, _ = s.state_device_ptr()
+    n2, occ = api().observe(ctx, 28, "c64", torch.from_numpy(s.state()).cuda())
+    assert abs(n2 - 1.0) <= 1e-5
+    assert np.all(occ >= -1e-7) and np.all(occ <= 1 + 1e-6)
+
+
+# ---------------------------------------------------------------------------
+# Observables and sampling
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n,prec", [(1, "c64"), (7, "c128"), (13, "c64"), (16, "c128"), (21, "c64")])
+def test_observe_matches_oracle(ctx, n, prec):
+    x = rand_state_gpu(n, prec, seed=7 * n)
+    n2, occ = api().observe(ctx, n, prec, x)
+    xh = x.cpu().numpy()
+    ref = O.occupations(xh)
+    p = xh.real.astype(np.float64) ** 2 + xh.imag.astype(np.float64) ** 2
+    assert abs(n2 - p.sum()) <= 1e-12
+    assert np.max(np.abs(occ - ref)) <= 1e-12
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+def test_sampling_matches_oracle_inverse_cdf(ctx, prec):
+    n = 10
+    x = rand_state_gpu(n, prec, seed=3)
+    shots, seed = 5000, 2024
+    got = api().sample(ctx, n, prec, x, shots, seed)
+    xh = x.cpu().numpy()
+    ref = O.sample_bitstrings(xh, shots, seed)
+    mism = np.nonzero(got != ref)[0]
+    # only shots whose uniform sits within rounding of a cdf boundary may differ
+    p = xh.real.astype(np.float64) ** 2 + xh.imag.astype(np.float64) ** 2
+    cdf = np.cumsum(p)
+    for s in mism:
+        u = O.shot_uniform(seed, int(s)) * cdf[-1]
+        assert np.min(np.abs(cdf - u)) <= 1e-12
+    assert len(mism) <= 2
+
+
+def test_sampling_distribution_large(ctx):
+    n = 20
+    x = rand_state_gpu(n, "c64", seed=11)
+    p = (x.abs() ** 2).double().cpu().numpy()
+    coarse = p.reshape(64, -1).sum(axis=1)
+    got = api().sample(ctx, n, "c64", x, 200000, 9)
+    counts = np.bincount((got >> np.uint64(n - 6)).astype(np.int64), minlength=64) / 200000
+    assert 0.5 * np.sum(np.abs(counts - coarse / coarse.sum())) < 0.01
+
+
+# ---------------------------------------------------------------------------
+# Errors and the whole-solve entry point
+# ---------------------------------------------------------------------------
+
+def test_run_entry_and_errors(ctx):
+    A = api()
+    prob = W.rabi_chain(6, 6.0, t_ns=200)
+    r = A.run(ctx, prob, 10, "c128", obs_stride=5)
+    ref, occ_ref = oracle_evolve(prob, 10)
+    assert O.infidelity(r.state(), ref) <= 1e-10
+    occ = r.occupations()
+    assert occ.shape == (1 + 20 // 5, 6)
+    assert np.max(np.abs(occ[-1] - occ_ref[-1])) <= 1e-10
+    samples = r.sample(1000, 5)
+    assert samples.max() < 64
+    st = r.stats()
+    assert st["steps"] == 20 and st["krylov_iterations"] >= 20
+    r.close()
+    bad = W.Problem(np.array([[0.0, 0.0], [0.0, 0.0]]), 1.0, 10, np.ones(10), np.zeros(10))
+    with pytest.raises(A.RsvError) as e:
+        A.run(ctx, bad, 10, "c64")
+    assert e.value.code == -6
+    with pytest.raises(A.RsvError):
+        A.run(ctx, prob, 0, "c64")
+    zero = np.zeros(64, dtype=np.complex128)
+    with pytest.raises(A.RsvError):
+        A.run(ctx, prob, 10, "c128", initial_state=zero)
+
+
+def test_arena_admission(ctx):
+    A = api()
+    small = A.Context(0, arena_bytes=64 << 20)
+    prob = W.rabi_chain(8, 6.0, t_ns=50)
+    r = A.run(small, prob, 10, "c64")
+    r.close()
+    big = W.random_box(seed=3, n=22, t_ns=10)
+    with pytest.raises(A.RsvError) as e:
+        A.Solver(small, big, 5, "c128", m_max=30)
+    assert e.value.code == -2
+    small.close()

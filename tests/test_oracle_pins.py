@@ -378,3 +378,14 @@ def test_paper_memory_figures():
     state = bpa * 2 ** int(n)
     assert state / 1e9 == pytest.approx(gb, rel=0.1)
     assert (state * (kv + 1) + 8 * 2 ** int(n)) / 1e9 < max_gb
+
+
+def test_hamiltonian_rows_match_dense():
+    rng = np.random.Generator(np.random.PCG64(77))
+    n = 6
+    V = O.pair_interactions(W.random_register(rng, n, 18.0), W.C6_DEFAULT)
+    om, de, ph = rng.uniform(0, 7, n), rng.normal(0, 3, n), rng.uniform(-3, 3, n)
+    H = O.dense_hamiltonian(V, om, de, ph)
+    x = rng.standard_normal(2 ** n) + 1j * rng.standard_normal(2 ** n)
+    idx = [0, 1, 17, 40, 63]
+    assert np.allclose(O.hamiltonian_rows(idx, x, V, om, de, ph), (H @ x)[idx], atol=1e-10)
