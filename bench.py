@@ -202,15 +202,17 @@ def ours(args):
     stream = torch.cuda.current_stream()
     solver = api.Solver(ctx, prob, DT_NS, "c64", m_max=M_MAX, obs_stride=1)
     total_steps = solver.progress()[1]
-    need = args.warmup + args.steps
-    if need > total_steps:
-        raise SystemExit(f"warmup + steps must be <= {total_steps}")
+    if max(args.warmup, args.steps) > total_steps:
+        raise SystemExit(f"warmup and steps must be <= {total_steps}")
 
     def barrier():
         if ws > 1:
             torch.distributed.barrier()
 
+    # warm up, then rewind so the timed steps are steps 0..K-1, the same ones
+    # the end-to-end run below covers
     solver.step(args.warmup)
+    solver.rewind()
     it0 = solver.stats()["krylov_iterations"]
     l0 = solver.stats()["kernel_launches"]
     solver.set_profiling(True)
@@ -335,6 +337,30 @@ def ours(args):
     return 0
 
 
+def profile_case(n_atoms: int):
+    """A small run of the same kernels for ncu captures: the random-box workload
+    at n_atoms (default 25: 256 MiB complex64 vectors, above L2), m_max = 8, two
+    time steps, then two pure matvecs. About 3 GB of device memory."""
+    import torch
+    from paper_2510_09813_b300 import api
+    from paper_2510_09813_b300 import workloads as W
+    prob = W.random_box(seed=3, n=n_atoms, t_ns=2 * DT_NS)
+    ctx = api.Context(0)
+    s = api.Solver(ctx, prob, DT_NS, "c64", m_max=8, obs_stride=1)
+    s.run_to_end()
+    st = s.stats()
+    s.close()
+    x = torch.zeros(2 ** n_atoms, dtype=torch.complex64, device="cuda")
+    x.real.normal_()
+    y = torch.empty_like(x)
+    V = api.pair_energies(prob.positions, prob.c6)
+    for _ in range(2):
+        api.apply_hamiltonian(ctx, n_atoms, "c64", V, prob.omega[:, 0], prob.delta[:, 0], None, x, y)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": n_atoms, "stats": st}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -342,7 +368,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-case", type=int, default=0, metavar="N",
+                    help="run the small ncu case at N atoms instead of the benchmark")
     args = ap.parse_args()
+    if args.profile_case:
+        return profile_case(args.profile_case)
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
     if args.impl == "reference":

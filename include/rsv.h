@@ -120,9 +120,15 @@ typedef struct {
 
 /* Creates a context on CUDA device `device`. arena_bytes > 0 caps the device
  * memory the context may hold (solvers beyond it fail with
- * RSV_ERR_OUT_OF_MEMORY); 0 means no cap. `cuda_stream` (a cudaStream_t) may
- * be NULL, in which case the context creates and owns a stream. */
+ * RSV_ERR_OUT_OF_MEMORY); 0 means no cap. `cuda_stream` (a cudaStream_t) is the
+ * stream all of the context's work is ordered on; pass cudaStreamLegacy
+ * ((cudaStream_t)0x1) to share the legacy default stream with other code.
+ * NULL makes the context create and own a non-blocking stream, which does NOT
+ * wait for work other libraries queue on the default stream: callers that
+ * hand in device buffers written elsewhere must then synchronise themselves. */
 RSV_API rsv_status rsv_create(rsv_ctx** out, int32_t device, size_t arena_bytes, void* cuda_stream);
+/* Destroys a context after its stream drains. Solvers and results still open
+ * on it are freed first; their handles become invalid. */
 RSV_API void rsv_destroy(rsv_ctx* ctx);
 /* Message of the calling thread's last failed call ("" if none). Valid until
  * the thread's next rsv_* call. */
@@ -191,6 +197,10 @@ RSV_API void rsv_solver_destroy(rsv_solver* s);
  * into Krylov restarts when m_max is reached. Records <n_i> per obs_stride.
  * Returns after the last step's work is complete on the device. */
 RSV_API rsv_status rsv_solver_step(rsv_solver* s, int32_t n_steps);
+/* Returns to t = 0: the state is reset to the problem's initial state, the
+ * step counter and the recorded occupations to empty (row 0 is re-recorded).
+ * Statistics keep accumulating. */
+RSV_API rsv_status rsv_solver_rewind(rsv_solver* s);
 /* Steps done so far and steps in the sequence. */
 RSV_API rsv_status rsv_solver_progress(const rsv_solver* s, int32_t* done, int32_t* total);
 /* Borrowed device pointer to the current state (2^n amplitudes), valid until

@@ -83,6 +83,7 @@ def lib():
             "rsv_solver_destroy": (None, [P]),
             "rsv_solver_step": (I32, [P, I32]),
             "rsv_solver_progress": (I32, [P, C.POINTER(I32), C.POINTER(I32)]),
+            "rsv_solver_rewind": (I32, [P]),
             "rsv_solver_state_device": (I32, [P, C.POINTER(P), C.POINTER(SZ)]),
             "rsv_solver_get_state": (I32, [P, P, SZ]),
             "rsv_solver_set_state": (I32, [P, P, SZ]),

@@ -7,11 +7,15 @@ stream unless given another one.
 from __future__ import annotations
 
 import ctypes as C
+import weakref
 
 import numpy as np
 
 from . import _lib as L
 from ._lib import RSV_C64, RSV_C128, RsvError, amp_dtype, check, precision_code  # noqa: F401
+
+
+CUDA_STREAM_LEGACY = 0x1  # cudaStreamLegacy handle value
 
 
 def _torch():
@@ -29,16 +33,28 @@ class Context:
             stream = torch.cuda.current_stream(device).cuda_stream
         elif hasattr(stream, "cuda_stream"):
             stream = stream.cuda_stream
+        if not stream:
+            # torch's default stream is the legacy NULL stream; name it explicitly
+            # (cudaStreamLegacy) so the library orders its work with torch's.
+            stream = CUDA_STREAM_LEGACY
         self.device = device
         self._h = C.c_void_p()
+        self._children = weakref.WeakSet()  # solvers/results to close before the context
         check(L.lib().rsv_create(C.byref(self._h), int(device), int(arena_bytes), C.c_void_p(stream)))
 
     @property
     def handle(self):
+        if not self._h:
+            raise RuntimeError("context is closed")
         return self._h
+
+    def _adopt(self, child):
+        self._children.add(child)
 
     def close(self):
         if self._h:
+            for ch in list(self._children):
+                ch.close()
             L.lib().rsv_destroy(self._h)
             self._h = C.c_void_p()
 
@@ -138,6 +154,7 @@ class Solver:
         self._h = C.c_void_p()
         check(L.lib().rsv_solver_create(ctx.handle, C.byref(self._pa.struct), C.byref(self._cfg),
                                         C.byref(self._h)))
+        ctx._adopt(self)
 
     def step(self, n_steps: int):
         check(L.lib().rsv_solver_step(self._h, int(n_steps)))
@@ -146,6 +163,10 @@ class Solver:
         d, t = C.c_int32(), C.c_int32()
         check(L.lib().rsv_solver_progress(self._h, C.byref(d), C.byref(t)))
         return d.value, t.value
+
+    def rewind(self):
+        """Back to t = 0 and the initial state."""
+        check(L.lib().rsv_solver_rewind(self._h))
 
     def run_to_end(self):
         d, t = self.progress()
@@ -208,8 +229,10 @@ class Solver:
 class Result:
     """rsv_result of a whole solve."""
 
-    def __init__(self, h, n, precision):
+    def __init__(self, ctx, h, n, precision):
+        self.ctx = ctx
         self._h, self.n, self.precision = h, n, precision
+        ctx._adopt(self)
 
     def state(self) -> np.ndarray:
         out = np.empty(2 ** self.n, dtype=amp_dtype(self.precision))
@@ -255,4 +278,4 @@ def run(ctx: Context, problem, dt_ns: int, precision="c128", krylov_tol=0.0, m_m
     cfg = L.make_config(dt_ns, precision, krylov_tol, m_max, max_substeps, obs_stride)
     h = C.c_void_p()
     check(L.lib().rsv_run(ctx.handle, C.byref(pa.struct), C.byref(cfg), C.byref(h)))
-    return Result(h, pa.n, precision_code(precision))
+    return Result(ctx, h, pa.n, precision_code(precision))

@@ -1,6 +1,7 @@
 // Host-side declarations of the kernel launchers (internal to the library).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -8,7 +9,14 @@
 
 namespace rsv {
 
-// Geometry and buffers of one streaming tile pass (see tile_kernels.cu).
+// Streaming tile pass geometry (tile_kernels.cu).
+constexpr int kTileBitsF = 12;  // complex64 tile: 2^12 amplitudes = 32 KiB
+constexpr int kTileBitsD = 11;  // complex128 tile: 2^11 amplitudes = 32 KiB
+constexpr int kConsumerWarps = 16;
+constexpr int kConsumers = kConsumerWarps * 32;
+constexpr int kTileThreads = kConsumers;       // warp 0 also issues the TMA loads
+constexpr int kStages = 3;                     // shared-memory ring depth (2 tiles per stage)
+
 struct TileArgs {
   int n;         // atoms = state bits
   int L;         // tile bits
@@ -16,8 +24,8 @@ struct TileArgs {
   int a;         // tile bits [c, L) are amplitude bits [a, a + L - c)
   int f2;        // first amplitude bit of the top fixed range (a + L - c)
   int nF2;       // bits in the top fixed range (n - f2)
-  int nG;        // lowest nG bits of the top range resolved by partner loads through L2
-  int kt;        // thread bits of the tile layout (<= 8)
+  int nG;        // lowest nG bits of the top range resolved by partner loads through L2 (<= 8)
+  int kt;        // consumer-thread bits of the tile layout (<= 9)
   int64_t num_tiles;
   const StepParams* sp;  // device
   const double* vmat;    // device [kMaxAtoms][kMaxAtoms], FP64, by bit position
@@ -28,6 +36,22 @@ struct TileArgs {
   void* out;
   const KState* ks;
   double* partials;      // [grid][3]
+  int* err;              // device error word: bit 0 = a bounded wait timed out
+  const double* diag;    // first pass: [num_tiles][kDiagStride] rows of w_q (q < L) and E_hi at [15]
+};
+
+// Per-tile diagonal decomposition rows (diag_kernels.cu): for the contiguous
+// tile tau (amplitude bits >= L fixed to the bits of tau),
+//   row[q] = w_q = sum_{r >= L} V_qr tau_r - delta_q   (q < L)
+//   row[15] = E_hi = sum_{L <= q < r} V_qr tau_q tau_r - sum_{q >= L} delta_q tau_q
+constexpr int kDiagStride = 16;
+cudaError_t launch_diag_table(const StepParams* sp, const double* vmat, int n, int L, int64_t num_tiles, double* out,
+                              cudaStream_t stream);
+
+// Tensor maps of the strided pass's two input tiles.
+struct TileMaps {
+  CUtensorMap x;
+  CUtensorMap z;
 };
 
 enum class TileMode {
@@ -38,7 +62,10 @@ enum class TileMode {
   kLanczosSecond,  // + high flips, reductions
 };
 
-cudaError_t launch_tile(const TileArgs& args, TileMode mode, bool c64, bool phi, int grid, cudaStream_t stream);
+cudaError_t launch_tile(const TileArgs& args, const TileMaps* maps, TileMode mode, bool c64, bool phi, int grid,
+                        cudaStream_t stream);
+// Tensor map over a state vector for the strided-pass tile geometry `g`.
+bool encode_tile_map(CUtensorMap* out, const void* base, const TileArgs& g, bool c64);
 
 // Krylov control kernels (krylov_kernels.cu).
 struct ScalarArgs {

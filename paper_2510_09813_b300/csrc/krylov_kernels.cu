@@ -245,13 +245,25 @@ __global__ void __launch_bounds__(kThreads) scalar_kernel(const ScalarArgs A) {
       status = kDone;
       tau_take = tau_rem;
     } else if (m >= A.m_max) {
-      double t = tau_rem;
+      // Largest t <= tau_rem whose estimate meets tol: halve until it does,
+      // then refine between t and 2t by bisection in log(t).
+      double t = tau_rem, t_bad = tau_rem;
       for (int it = 0; it < 64; ++it) {
+        t_bad = t;
         t *= 0.5;
         cheb_expm_e1(s_al, s_be, m, t, s_ur, s_ui, s_w);
         err = beta * hypot(s_ur[m - 1], s_ui[m - 1]);
         if (err <= A.tol) break;
       }
+      for (int it = 0; it < 4; ++it) {
+        const double tm = sqrt(t * t_bad);
+        cheb_expm_e1(s_al, s_be, m, tm, s_ur, s_ui, s_w);
+        const double em = beta * hypot(s_ur[m - 1], s_ui[m - 1]);
+        if (em <= A.tol) t = tm;
+        else t_bad = tm;
+      }
+      cheb_expm_e1(s_al, s_be, m, t, s_ur, s_ui, s_w);
+      err = beta * hypot(s_ur[m - 1], s_ui[m - 1]);
       status = kDonePartial;
       tau_take = t;
     }

@@ -45,7 +45,9 @@ struct KState {
   double norm2;                  // |psi|^2 of the current state
   int64_t total_iterations;
   int64_t total_substeps;
-  double pad_[7];
+  int32_t error;                 // set by kernels whose bounded waits timed out
+  int32_t pad_i;
+  double pad_[6];
   // --- values consumed by the next "first" pass ---
   double form_a;                 // alpha_{j-1} (0 for j = 0)
   double form_s;                 // 1 / beta_j (1 / |psi| for j = 0)
@@ -57,7 +59,7 @@ struct KState {
   double coef_im[kMaxKrylov];
 };
 constexpr int kStatusBytes = 128;
-static_assert(sizeof(int32_t) * 4 + sizeof(double) * 5 + sizeof(int64_t) * 2 + sizeof(double) * 7 == kStatusBytes,
+static_assert(sizeof(int32_t) * 6 + sizeof(double) * 5 + sizeof(int64_t) * 2 + sizeof(double) * 6 == kStatusBytes,
               "status block layout");
 
 template <typename Real>

@@ -14,6 +14,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <set>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -45,12 +46,15 @@ rsv_status fail(rsv_status code, const std::string& msg) {
     if (s_ != RSV_OK) return s_;     \
   } while (0)
 
-constexpr int kTileBitsC64 = 13;
-constexpr int kTileBitsC128 = 12;
+constexpr int kTileBitsC64 = kTileBitsF;
+constexpr int kTileBitsC128 = kTileBitsD;
 constexpr int kMinSegmentBits = 4;   // contiguous amplitude bits of the strided pass
 constexpr int kMaxSingleGBits = 2;   // bits above the tile resolved in the single pass
+constexpr int kMaxGBits = 12;        // partner bits through L2 a pass can take
 
 int64_t amp_bytes(int precision) { return precision == RSV_C64 ? 8 : 16; }
+
+int* err_ptr(KState* ks) { return reinterpret_cast<int*>(reinterpret_cast<char*>(ks) + offsetof(KState, error)); }
 
 // ---------------------------------------------------------------------------
 // Device arena: first-fit free list with coalescing over one allocation, or
@@ -165,6 +169,9 @@ struct rsv_ctx {
   double* d_occ = nullptr;
   KState* h_ks = nullptr;    // pinned
   std::mutex mu;
+  // open objects, freed by rsv_destroy if the caller did not free them first
+  std::set<rsv_solver*> solvers;
+  std::set<rsv_result*> results;
 };
 
 namespace {
@@ -191,7 +198,7 @@ Plan make_plan(int n, bool c64, int num_sms) {
     t.f2 = a + (L - c);
     t.nF2 = n - t.f2;
     t.nG = nG;
-    t.kt = std::min(8, L - v);
+    t.kt = std::min(9, L - v);
     t.num_tiles = int64_t(1) << (n - L);
   };
   if (n <= lt) {
@@ -203,11 +210,11 @@ Plan make_plan(int n, bool c64, int num_sms) {
     const int h = std::min(n - lt, lt - kMinSegmentBits);
     const int c = lt - h;
     geom(p.b, lt, c, lt, 0);
-    p.b.nG = p.b.nF2;
+    p.b.nG = p.b.nF2;  // callers check nG <= kMaxGBits
     p.two_pass = true;
   }
   p.L_a = p.a.L;
-  const int resident = 2 * num_sms;
+  const int resident = num_sms;  // persistent: one CTA per SM
   p.grid_a = (int)std::min<int64_t>(p.a.num_tiles, resident);
   p.grid_b = p.two_pass ? (int)std::min<int64_t>(p.b.num_tiles, resident) : 0;
   const int T = std::min(n, v + 8 + 4);
@@ -315,8 +322,8 @@ bool any_phi(const std::vector<StepParams>& sp, int n) {
 }
 
 // Launch one streaming pass.
-rsv_status run_pass(rsv_ctx* ctx, TileArgs args, TileMode mode, bool c64, bool phi, int grid) {
-  cudaError_t e = launch_tile(args, mode, c64, phi, grid, ctx->stream);
+rsv_status run_pass(rsv_ctx* ctx, TileArgs args, const TileMaps* maps, TileMode mode, bool c64, bool phi, int grid) {
+  cudaError_t e = launch_tile(args, maps, mode, c64, phi, grid, ctx->stream);
   if (e != cudaSuccess) return fail(RSV_ERR_CUDA, std::string("tile kernel launch: ") + cudaGetErrorString(e));
   return RSV_OK;
 }
@@ -341,10 +348,13 @@ struct rsv_solver {
   StepParams* d_sp = nullptr;
   double* d_vmat = nullptr;
   void* d_qtab = nullptr;
+  double* d_diag = nullptr;  // per-tile diagonal rows of the current step
   void* d_psi = nullptr;
   void* d_u[2] = {nullptr, nullptr};
   std::vector<void*> basis;
   void** d_basis = nullptr;
+  std::vector<CUtensorMap> map_basis;  // strided-pass tensor maps over basis[j]
+  CUtensorMap map_u[2];                // ... over the two work vectors
   KState* d_ks = nullptr;
   double* d_part = nullptr;
   double* d_cpart = nullptr;
@@ -364,6 +374,30 @@ struct rsv_solver {
   };
   std::vector<Pending> pending;
   std::vector<cudaEvent_t> event_pool;
+  std::vector<char> init_host;  // caller's initial state (empty: |0...0>)
+
+  // State <- initial state, step counter and recorded rows <- 0, row 0 recorded.
+  rsv_status reset_to_initial() {
+    const size_t vbytes = (size_t)dim * amp_bytes(precision);
+    if (!init_host.empty()) {
+      RSV_CUDA(cudaMemcpyAsync(d_psi, init_host.data(), vbytes, cudaMemcpyHostToDevice, ctx->stream));
+    } else {
+      RSV_CUDA(cudaMemsetAsync(d_psi, 0, vbytes, ctx->stream));
+      const double one_d[2] = {1.0, 0.0};
+      const float one_f[2] = {1.f, 0.f};
+      RSV_CUDA(cudaMemcpyAsync(d_psi, c64 ? (const void*)one_f : (const void*)one_d, c64 ? sizeof(one_f) : sizeof(one_d),
+                               cudaMemcpyHostToDevice, ctx->stream));
+    }
+    std::vector<char> zero_ks(sizeof(KState), 0);
+    RSV_CUDA(cudaMemcpyAsync(d_ks, zero_ks.data(), sizeof(KState), cudaMemcpyHostToDevice, ctx->stream));
+    done = 0;
+    rows = 0;
+    last_m = 0;
+    RSV_TRY(observe_into_partials());
+    RSV_TRY(record_row());
+    RSV_CUDA(cudaStreamSynchronize(ctx->stream));
+    return RSV_OK;
+  }
 
   rsv_status alloc(size_t bytes, void** out) {
     RSV_TRY(ctx->arena.alloc(bytes, out));
@@ -477,6 +511,8 @@ struct rsv_solver {
     a.qtab = d_qtab;
     a.ks = d_ks;
     a.partials = d_part;
+    a.err = err_ptr(d_ks);
+    a.diag = d_diag;
     return a;
   }
 
@@ -494,15 +530,18 @@ struct rsv_solver {
     const double first_bytes = vec_bytes() * (j > 0 ? 4 : 3);
     if (!plan.two_pass) {
       RSV_TRY(launch(RSV_KERNEL_PASS_FIRST, first_bytes,
-                     [&] { return launch_tile(a, TileMode::kLanczosSingle, c64, phi, plan.grid_a, ctx->stream); }));
+                     [&] { return launch_tile(a, nullptr, TileMode::kLanczosSingle, c64, phi, plan.grid_a, ctx->stream); }));
     } else {
       RSV_TRY(launch(RSV_KERNEL_PASS_FIRST, first_bytes,
-                     [&] { return launch_tile(a, TileMode::kLanczosFirst, c64, phi, plan.grid_a, ctx->stream); }));
+                     [&] { return launch_tile(a, nullptr, TileMode::kLanczosFirst, c64, phi, plan.grid_a, ctx->stream); }));
       TileArgs b = base_args(plan.b, step);
       b.xin = basis[j];
       b.out = u_out;
       RSV_TRY(launch(RSV_KERNEL_PASS_SECOND, vec_bytes() * 3,
-                     [&] { return launch_tile(b, TileMode::kLanczosSecond, c64, phi, plan.grid_b, ctx->stream); }));
+                     [&] {
+                       TileMaps maps{map_basis[j], map_u[j & 1]};
+                       return launch_tile(b, &maps, TileMode::kLanczosSecond, c64, phi, plan.grid_b, ctx->stream);
+                     }));
     }
     return RSV_OK;
   }
@@ -511,6 +550,9 @@ struct rsv_solver {
     const int k = done;
     const double tau = h_sp[k].tau;
     RSV_TRY(begin(tau, 0, nullptr));
+    RSV_TRY(launch(RSV_KERNEL_CONTROL, 0.0, [&] {
+      return launch_diag_table(d_sp + k, d_vmat, n, plan.a.L, plan.a.num_tiles, d_diag, ctx->stream);
+    }));
     const int m_max = cfg.m_max;
     int restarts = 0;
     while (true) {
@@ -530,6 +572,7 @@ struct rsv_solver {
         RSV_TRY(launch(RSV_KERNEL_CONTROL, 0.0, [&] { return launch_scalar(sa, ctx->stream); }));
         if (j + 1 >= check_from) {
           RSV_TRY(read_status());
+          if (h_ks->error) return fail(RSV_ERR_TIMEOUT, "a device-side wait timed out (kernel aborted)");
           if (h_ks->status == kIdle) return fail(RSV_ERR_INVALID_ARG, "state has zero norm");
           if (h_ks->status != kContinue) {
             finished = true;
@@ -618,6 +661,9 @@ void rsv_destroy(rsv_ctx* ctx) {
   if (!ctx) return;
   cudaSetDevice(ctx->device);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  // free what the caller left open (their handles become invalid)
+  while (!ctx->results.empty()) rsv_result_free(*ctx->results.begin());
+  while (!ctx->solvers.empty()) rsv_solver_destroy(*ctx->solvers.begin());
   ctx->arena.release(ctx->d_sp);
   ctx->arena.release(ctx->d_vmat);
   ctx->arena.release(ctx->d_qtab);
@@ -711,27 +757,50 @@ rsv_status rsv_apply_hamiltonian(rsv_ctx* ctx, int32_t n_atoms, int32_t precisio
     qd = q_table<double>(vb, plan.L_a);
     RSV_CUDA(cudaMemcpyAsync(ctx->d_qtab, qd.data(), qd.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
   }
+  RSV_CUDA(cudaMemsetAsync(err_ptr(ctx->d_ks), 0, sizeof(int), ctx->stream));
+  double* d_diag = nullptr;
+  RSV_TRY(ctx->arena.alloc(sizeof(double) * kDiagStride * plan.a.num_tiles, (void**)&d_diag));
+  struct DiagGuard {
+    rsv_ctx* c;
+    double* p;
+    ~DiagGuard() {
+      cudaStreamSynchronize(c->stream);
+      c->arena.release(p);
+    }
+  } diag_guard{ctx, d_diag};
+  {
+    cudaError_t e = launch_diag_table(ctx->d_sp, ctx->d_vmat, n, plan.a.L, plan.a.num_tiles, d_diag, ctx->stream);
+    if (e != cudaSuccess) return fail(RSV_ERR_CUDA, std::string("diag table: ") + cudaGetErrorString(e));
+  }
   TileArgs a = plan.a;
   a.sp = ctx->d_sp;
   a.vmat = ctx->d_vmat;
   a.qtab = ctx->d_qtab;
   a.ks = ctx->d_ks;
   a.partials = ctx->d_part;
+  a.err = err_ptr(ctx->d_ks);
+  a.diag = d_diag;
   a.xin = x_dev;
   a.out = y_dev;
-  RSV_TRY(run_pass(ctx, a, TileMode::kMatvecFirst, c64, has_phi, plan.grid_a));
+  RSV_TRY(run_pass(ctx, a, nullptr, TileMode::kMatvecFirst, c64, has_phi, plan.grid_a));
   if (plan.two_pass) {
     TileArgs b = plan.b;
     b.sp = ctx->d_sp;
     b.vmat = ctx->d_vmat;
     b.ks = ctx->d_ks;
     b.partials = ctx->d_part;
+    b.err = err_ptr(ctx->d_ks);
     b.xin = x_dev;
     b.out = y_dev;
-    RSV_TRY(run_pass(ctx, b, TileMode::kMatvecSecond, c64, has_phi, plan.grid_b));
+    TileMaps maps;
+    if (!encode_tile_map(&maps.x, x_dev, plan.b, c64) || !encode_tile_map(&maps.z, y_dev, plan.b, c64))
+      return fail(RSV_ERR_CUDA, "tensor map encoding failed");
+    RSV_TRY(run_pass(ctx, b, &maps, TileMode::kMatvecSecond, c64, has_phi, plan.grid_b));
   }
   // keep host staging alive until the copies are done
+  RSV_CUDA(cudaMemcpyAsync(ctx->h_ks, ctx->d_ks, kStatusBytes, cudaMemcpyDeviceToHost, ctx->stream));
   RSV_CUDA(cudaStreamSynchronize(ctx->stream));
+  if (ctx->h_ks->error) return fail(RSV_ERR_TIMEOUT, "a device-side wait timed out (kernel aborted)");
   return RSV_OK;
 }
 
@@ -868,6 +937,7 @@ rsv_status rsv_solver_create(rsv_ctx* ctx, const rsv_problem* problem, const rsv
   A(sizeof(StepParams) * s->nsteps, (void**)&s->d_sp);
   A(sizeof(double) * kMaxAtoms * kMaxAtoms, (void**)&s->d_vmat);
   A(amp_bytes(cfg.precision) / 2 * (size_t(1) << s->plan.L_a), &s->d_qtab);
+  A(sizeof(double) * kDiagStride * s->plan.a.num_tiles, (void**)&s->d_diag);
   A(vbytes, &s->d_psi);
   A(vbytes, &s->d_u[0]);
   A(vbytes, &s->d_u[1]);
@@ -886,6 +956,17 @@ rsv_status rsv_solver_create(rsv_ctx* ctx, const rsv_problem* problem, const rsv
   if (e != cudaSuccess) {
     delete s;
     return fail(RSV_ERR_CUDA, std::string("cudaMallocHost: ") + cudaGetErrorString(e));
+  }
+  if (s->plan.two_pass) {
+    s->map_basis.resize(cfg.m_max);
+    bool ok = true;
+    for (int k = 0; k < cfg.m_max; ++k) ok = ok && encode_tile_map(&s->map_basis[k], s->basis[k], s->plan.b, s->c64);
+    ok = ok && encode_tile_map(&s->map_u[0], s->d_u[0], s->plan.b, s->c64) &&
+         encode_tile_map(&s->map_u[1], s->d_u[1], s->plan.b, s->c64);
+    if (!ok) {
+      delete s;
+      return fail(RSV_ERR_CUDA, "tensor map encoding failed");
+    }
   }
   auto fin = [&](rsv_status r) {
     if (r != RSV_OK) delete s;
@@ -913,33 +994,33 @@ rsv_status rsv_solver_create(rsv_ctx* ctx, const rsv_problem* problem, const rsv
       return fin(fail(RSV_ERR_CUDA, "upload failed"));
     cudaStreamSynchronize(ctx->stream);
   }
-  // initial state
   if (problem->initial_state) {
-    if (cudaMemcpyAsync(s->d_psi, problem->initial_state, vbytes, cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess)
-      return fin(fail(RSV_ERR_CUDA, "initial state upload failed"));
-  } else {
-    if (cudaMemsetAsync(s->d_psi, 0, vbytes, ctx->stream) != cudaSuccess)
-      return fin(fail(RSV_ERR_CUDA, "memset failed"));
-    if (s->c64) {
-      const float one[2] = {1.f, 0.f};
-      if (cudaMemcpyAsync(s->d_psi, one, sizeof(one), cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess)
-        return fin(fail(RSV_ERR_CUDA, "upload failed"));
-    } else {
-      const double one[2] = {1.0, 0.0};
-      if (cudaMemcpyAsync(s->d_psi, one, sizeof(one), cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess)
-        return fin(fail(RSV_ERR_CUDA, "upload failed"));
-    }
+    const char* p = static_cast<const char*>(problem->initial_state);
+    s->init_host.assign(p, p + vbytes);
   }
-  if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return fin(fail(RSV_ERR_CUDA, "sync failed"));
-  rsv_status r = s->observe_into_partials();
-  if (r == RSV_OK) r = s->record_row();
-  if (r == RSV_OK && cudaStreamSynchronize(ctx->stream) != cudaSuccess) r = fail(RSV_ERR_CUDA, "sync failed");
+  rsv_status r = s->reset_to_initial();
   if (r != RSV_OK) return fin(r);
+  ctx->solvers.insert(s);
   *out = s;
   return RSV_OK;
 }
 
-void rsv_solver_destroy(rsv_solver* s) { delete s; }
+rsv_status rsv_solver_rewind(rsv_solver* s) {
+  g_last_error.clear();
+  if (!s) return fail(RSV_ERR_INVALID_ARG, "NULL solver");
+  std::lock_guard<std::mutex> lk(s->ctx->mu);
+  cudaSetDevice(s->ctx->device);
+  return s->reset_to_initial();
+}
+
+void rsv_solver_destroy(rsv_solver* s) {
+  if (!s) return;
+  {
+    std::lock_guard<std::mutex> lk(s->ctx->mu);
+    s->ctx->solvers.erase(s);
+  }
+  delete s;
+}
 
 rsv_status rsv_solver_step(rsv_solver* s, int32_t n_steps) {
   g_last_error.clear();
@@ -1048,6 +1129,11 @@ rsv_status rsv_run(rsv_ctx* ctx, const rsv_problem* problem, const rsv_config* c
   }
   auto r = new rsv_result();
   r->solver = s;
+  {
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->solvers.erase(s);
+    ctx->results.insert(r);
+  }
   r->rows = s->rows;
   r->occ.resize((size_t)s->rows * s->n);
   int32_t rows = 0;
@@ -1092,7 +1178,11 @@ rsv_status rsv_result_stats(const rsv_result* r, rsv_stats* out) {
 
 void rsv_result_free(rsv_result* r) {
   if (!r) return;
-  rsv_solver_destroy(r->solver);
+  {
+    std::lock_guard<std::mutex> lk(r->solver->ctx->mu);
+    r->solver->ctx->results.erase(r);
+  }
+  delete r->solver;  // owned by the result, not in the context's solver set
   delete r;
 }
 

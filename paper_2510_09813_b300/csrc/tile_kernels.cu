@@ -2,357 +2,574 @@
 // Eq. (3)) and the Lanczos iteration built on it (Sec. III.A).
 //
 // H x is "apply the diagonal, then add the Omega-scaled bit-flip permutations"
-// (Sec. III.A). Here the diagonal is never stored: each tile rebuilds
+// (Sec. III.A). The diagonal is never stored: each tile rebuilds
 //     E(b) = sum_{q<r} V_qr b_q b_r - sum_q delta_q b_q
 // from FP64 pair energies as E_hi(tile) + sum_{q<L} w_q(tile) b_q + Q[b_lo].
 //
-// A tile is a 2^L-amplitude sub-cube of the state: tile bits [0,c) are the
-// amplitude bits [0,c) (contiguous in memory, for coalescing) and tile bits
-// [c,L) are amplitude bits [a, a+L-c). Every other bit is fixed per tile. The
-// tile is staged in shared memory, so flips of all L tile bits are resolved on
-// chip: the vector lane bit in registers, the 8 "thread" bits through shared
-// memory and the "register" bits inside each thread's register array. Flips of
-// the lowest nG fixed bits (G bits) read the partner tile through L2; tiles
-// that differ only in G bits are scheduled back to back so those partners are
-// L2 hits. A full matvec over N > L bits is one pass (N <= L + nG) or two
-// passes: a contiguous pass over bits [0, L) plus a strided pass over the rest.
+// Tiles. A tile is a 2^L-amplitude sub-cube of the state: tile bits [0,c) are
+// amplitude bits [0,c) (contiguous in memory) and tile bits [c,L) are amplitude
+// bits [a, a+L-c). The remaining bits are fixed per tile; the lowest nG of the
+// top fixed range are "G bits" whose partners are read from the neighbouring
+// tile through L2 (neighbours differ in the low bits of the tile index, so they
+// are processed at the same time by other CTAs). A full matvec is one pass when
+// the tile plus G bits cover the state, else two: a contiguous pass over bits
+// [0, L) that also adds the diagonal, and a strided pass over the rest.
 //
-// The Lanczos variant fuses, per amplitude: forming v_j = (u_{j-1} -
-// alpha_{j-1} v_{j-1}) / beta_j from the previous pass's output, writing v_j
-// into the Krylov basis, the matvec, the three-term subtraction -beta_j v_{j-1}
-// and the three reductions Re<v_j,u_j>, |u_j|^2, |v_j|^2 from which the scalar
-// kernel derives alpha_j and beta_{j+1} without another pass.
+// Execution. One persistent CTA of 16 warps per SM (4 per SM sub-partition, so
+// each thread may hold 128 registers). The CTA's input tiles stream into a
+// 3-stage shared-memory ring by TMA (1D bulk copies for contiguous tiles, tiled
+// tensor copies for strided ones) with mbarrier completion; warp 0 issues the
+// copies two tiles ahead before computing its own share. All warps compute from
+// shared memory and store results straight to global memory. Every flip partner
+// inside the tile is a 16-byte shared-memory load; complex64 arithmetic uses
+// packed FP32x2 FMAs. Every mbarrier wait is bounded.
+//
+// Lanczos fusion. The first pass forms v_j = (u_{j-1} - alpha_{j-1} v_{j-1}) /
+// beta_j in place from the staged tiles, writes v_j to the Krylov basis and
+// subtracts beta_j v_{j-1}; the last pass accumulates Re<v_j,u_j>, |u_j|^2 and
+// |v_j|^2, from which the scalar kernel derives alpha_j and beta_{j+1}.
+#include <type_traits>
+
 #include "kernels.h"
 #include "rsv_common.cuh"
+#include "tma.cuh"
 
 namespace rsv {
 
 template <typename Real>
-struct Lanes {
-  static constexpr int kLogVec = CplxT<Real>::kLogVec;
-  static constexpr int kNV = 1 << kLogVec;  // amplitudes per 16-byte vector
-  static constexpr int kR = 2 * kNV;         // reals per vector
+struct TileCfg {
+  static constexpr bool kF = std::is_same<Real, float>::value;
+  static constexpr int V = CplxT<Real>::kLogVec;  // log2 amplitudes per 16-byte vector
+  static constexpr int NV = 1 << V;
+  static constexpr int L = kF ? kTileBitsF : kTileBitsD;
+  static constexpr int KT = 9;               // consumer-thread bits of a full tile
+  static constexpr int KK = L - V - KT;      // register ("k") bits of a full tile
+  static constexpr int K = 1 << KK;          // vectors per consumer thread
+  static constexpr uint32_t kTileBytes = (1u << L) * 2u * sizeof(Real);
+};
+static_assert(TileCfg<float>::KK == 2 && TileCfg<double>::KK == 2, "tile layout");
+
+constexpr int kMaxG = 12;
+
+// ---- complex helpers -------------------------------------------------------
+// One 16-byte vector: complex64 = 2 amplitudes (two packed f32x2 words),
+// complex128 = 1 amplitude (two doubles).
+struct Vec {
+  unsigned long long w0, w1;
 };
 
-template <typename Real>
-__device__ __forceinline__ void load_vec(Real (&d)[Lanes<Real>::kR], const void* base, int64_t vidx) {
-  using vec = typename CplxT<Real>::vec;
-  vec v = reinterpret_cast<const vec*>(base)[vidx];
-  *reinterpret_cast<vec*>(d) = v;
+__device__ __forceinline__ Vec lds_vec(const void* base, int idx) {
+  const ulonglong2 v = reinterpret_cast<const ulonglong2*>(base)[idx];
+  return Vec{v.x, v.y};
 }
-template <typename Real>
-__device__ __forceinline__ void load_vec_cs(Real (&d)[Lanes<Real>::kR], const void* base, int64_t vidx) {
-  using vec = typename CplxT<Real>::vec;
-  vec v = __ldcs(reinterpret_cast<const vec*>(base) + vidx);
-  *reinterpret_cast<vec*>(d) = v;
+__device__ __forceinline__ void sts_vec(void* base, int idx, Vec v) {
+  reinterpret_cast<ulonglong2*>(base)[idx] = make_ulonglong2(v.w0, v.w1);
 }
-template <typename Real>
-__device__ __forceinline__ void store_vec(void* base, int64_t vidx, const Real (&s)[Lanes<Real>::kR]) {
-  using vec = typename CplxT<Real>::vec;
-  reinterpret_cast<vec*>(base)[vidx] = *reinterpret_cast<const vec*>(s);
+__device__ __forceinline__ Vec ldg_vec(const void* base, int64_t idx) {
+  const ulonglong2 v = __ldg(reinterpret_cast<const ulonglong2*>(base) + idx);
+  return Vec{v.x, v.y};
 }
-template <typename Real>
-__device__ __forceinline__ void store_vec_cs(void* base, int64_t vidx, const Real (&s)[Lanes<Real>::kR]) {
-  using vec = typename CplxT<Real>::vec;
-  __stcs(reinterpret_cast<vec*>(base) + vidx, *reinterpret_cast<const vec*>(s));
+__device__ __forceinline__ Vec ldcs_vec(const void* base, int64_t idx) {
+  const ulonglong2 v = __ldcs(reinterpret_cast<const ulonglong2*>(base) + idx);
+  return Vec{v.x, v.y};
 }
+__device__ __forceinline__ void stg_vec(void* base, int64_t idx, Vec v) {
+  reinterpret_cast<ulonglong2*>(base)[idx] = make_ulonglong2(v.w0, v.w1);
+}
+__device__ __forceinline__ double dbl(unsigned long long w) { return __longlong_as_double((long long)w); }
+__device__ __forceinline__ unsigned long long bits(double d) { return (unsigned long long)__double_as_longlong(d); }
 
-// o += coef * p for one complex amplitude; coef real unless PHI.
+// Coefficient of one flip in "apply" form. complex64: rr = (cr, cr), ii = (-ci, ci)
+// as packed pairs; complex128: cr, ci as doubles (stored in the same words).
+struct Coef {
+  unsigned long long rr, ii;
+};
+
 template <typename Real, bool PHI>
-__device__ __forceinline__ void cmac(Real& ore, Real& oim, Real cr, Real ci, Real pre, Real pim) {
-  if (PHI) {
-    ore = fma(cr, pre, ore);
-    ore = fma(-ci, pim, ore);
-    oim = fma(cr, pim, oim);
-    oim = fma(ci, pre, oim);
+__device__ __forceinline__ Coef make_coef(Real cr, Real ci) {
+  if constexpr (TileCfg<Real>::kF) {
+    return Coef{f2_pack(cr, cr), PHI ? f2_pack(-ci, ci) : 0ull};
   } else {
-    ore = fma(cr, pre, ore);
-    oim = fma(cr, pim, oim);
+    return Coef{bits(cr), bits(ci)};
   }
 }
 
-template <typename Real, int KK, bool LANCZOS, bool FIRST, bool LAST, bool PHI>
-__global__ void __launch_bounds__(kThreads, 2) tile_kernel(const TileArgs args) {
-  using L_ = Lanes<Real>;
-  using Acc = typename AccFor<Real>::type;
-  constexpr int V = L_::kLogVec;
-  constexpr int NV = L_::kNV;
-  constexpr int R = L_::kR;
-  constexpr int K = 1 << KK;
+// complex64 amplitude o += coef * p (packed re, im).
+template <bool PHI>
+__device__ __forceinline__ void cmac_word(unsigned long long& o, const Coef& c, unsigned long long p) {
+  f2_fma(o, c.rr, p);
+  if (PHI) {
+    float re, im;
+    f2_unpack(p, re, im);
+    f2_fma(o, c.ii, f2_pack(im, re));
+  }
+}
 
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  Real* sx = reinterpret_cast<Real*>(smem_raw);  // tile: [2^(L-V)] vectors of R reals
-  __shared__ double s_w[kMaxAtoms];
-  __shared__ double s_ehi;
-  __shared__ Real s_linreg[K];
-  __shared__ Real s_coef[kMaxAtoms][2][2];  // [amp bit][bit state of the target][re, im]
-  __shared__ double s_red[3 * (kThreads / 32)];
-
-  if (LANCZOS && args.ks->status != kContinue) return;
-
-  const int tid = threadIdx.x;
-  const int n = args.n, L = args.L, c = args.c, a = args.a, f2 = args.f2;
-  const int nF2 = args.nF2, nG = args.nG, kt = args.kt;
-  const bool active = tid < (1 << kt);
-  const StepParams* sp = args.sp;
-
-  if (tid < n) {
-    const double ho = sp->half_omega[tid];
+// o += coef * p on every amplitude of the vector.
+template <typename Real, bool PHI>
+__device__ __forceinline__ void cmac(Vec& o, const Coef& c, const Vec& p) {
+  if constexpr (TileCfg<Real>::kF) {
+    cmac_word<PHI>(o.w0, c, p.w0);
+    cmac_word<PHI>(o.w1, c, p.w1);
+  } else {
+    const double cr = dbl(c.rr), pr = dbl(p.w0), pi = dbl(p.w1);
+    double orr = fma(cr, pr, dbl(o.w0)), oi = fma(cr, pi, dbl(o.w1));
     if (PHI) {
-      double sn, cs;
-      sincos(sp->phi[tid], &sn, &cs);
-      // target bit 0: <0|h|1> = Omega/2 e^{+i phi}; target bit 1: <1|h|0> = Omega/2 e^{-i phi}
-      s_coef[tid][0][0] = (Real)(ho * cs);
-      s_coef[tid][0][1] = (Real)(ho * sn);
-      s_coef[tid][1][0] = (Real)(ho * cs);
-      s_coef[tid][1][1] = (Real)(-ho * sn);
-    } else {
-      s_coef[tid][0][0] = s_coef[tid][1][0] = (Real)ho;
-      s_coef[tid][0][1] = s_coef[tid][1][1] = (Real)0;
+      const double ci = dbl(c.ii);
+      orr = fma(-ci, pi, orr);
+      oi = fma(ci, pr, oi);
     }
+    o.w0 = bits(orr);
+    o.w1 = bits(oi);
   }
+}
 
-  double form_a = 0.0, form_s = 1.0, beta_prev = 0.0;
-  int jj = 0;
-  if (LANCZOS && FIRST) {
-    form_a = args.ks->form_a;
-    form_s = args.ks->form_s;
-    beta_prev = args.ks->beta_prev;
-    jj = args.ks->j;
+// o = s * x (real s) per amplitude; e0/e1 are the per-amplitude scales (complex64
+// has two amplitudes per vector, complex128 uses e0 only).
+template <typename Real>
+__device__ __forceinline__ Vec scale2(const Vec& x, Real e0, Real e1) {
+  if constexpr (TileCfg<Real>::kF) {
+    return Vec{f2_mul(f2_pack(e0, e0), x.w0), f2_mul(f2_pack(e1, e1), x.w1)};
+  } else {
+    return Vec{bits(e0 * dbl(x.w0)), bits(e0 * dbl(x.w1))};
   }
-  const Real fa = (Real)form_a, fs = (Real)form_s, bp = (Real)beta_prev;
-  const Real* qtab = reinterpret_cast<const Real*>(args.qtab);
+}
 
-  Acc r0, r1, r2;
-  const int64_t cmask = (int64_t(1) << c) - 1;
-  const int64_t f2mask = (int64_t(1) << nF2) - 1;
+// o += s * x (real s, same for every amplitude)
+template <typename Real>
+__device__ __forceinline__ void axpy(Vec& o, Real s, const Vec& x) {
+  if constexpr (TileCfg<Real>::kF) {
+    const unsigned long long ss = f2_pack(s, s);
+    f2_fma(o.w0, ss, x.w0);
+    f2_fma(o.w1, ss, x.w1);
+  } else {
+    o.w0 = bits(fma(s, dbl(x.w0), dbl(o.w0)));
+    o.w1 = bits(fma(s, dbl(x.w1), dbl(o.w1)));
+  }
+}
 
-  for (int64_t tile = blockIdx.x; tile < args.num_tiles; tile += gridDim.x) {
-    const int64_t base = ((tile >> nF2) << c) | ((tile & f2mask) << f2);
-    __syncthreads();  // previous tile's shared-memory readers are done
+// x = (u - a v) * s
+template <typename Real>
+__device__ __forceinline__ Vec form(const Vec& u, const Vec& v, Real a, Real s, bool has_v) {
+  Vec r = u;
+  if (has_v) axpy<Real>(r, -a, v);
+  return scale2<Real>(r, s, s);
+}
+
+// Re<x, o>, |o|^2, |x|^2 of one vector: four-term FP32 (or FP64) partials,
+// accumulated across vectors with the compensated accumulator.
+template <typename Real, typename Acc>
+__device__ __forceinline__ void reduce_vec(const Vec& x, const Vec& o, Acc& r0, Acc& r1, Acc& r2) {
+  if constexpr (TileCfg<Real>::kF) {
+    float x0, x1, x2, x3, o0, o1, o2, o3;
+    f2_unpack(x.w0, x0, x1);
+    f2_unpack(x.w1, x2, x3);
+    f2_unpack(o.w0, o0, o1);
+    f2_unpack(o.w1, o2, o3);
+    r0.add(fmaf(x3, o3, fmaf(x2, o2, fmaf(x1, o1, x0 * o0))));
+    r1.add(fmaf(o3, o3, fmaf(o2, o2, fmaf(o1, o1, o0 * o0))));
+    r2.add(fmaf(x3, x3, fmaf(x2, x2, fmaf(x1, x1, x0 * x0))));
+  } else {
+    const double x0 = dbl(x.w0), x1 = dbl(x.w1), o0 = dbl(o.w0), o1 = dbl(o.w1);
+    r0.dot(x0, o0);
+    r0.dot(x1, o1);
+    r1.dot(o0, o0);
+    r1.dot(o1, o1);
+    r2.dot(x0, x0);
+    r2.dot(x1, x1);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// The streaming pass.
+// ---------------------------------------------------------------------------
+template <typename Real, bool LANCZOS, bool FIRST, bool LAST, bool PHI>
+__global__ void __launch_bounds__(kTileThreads, 1)
+    tile_kernel(const TileArgs args, const __grid_constant__ TileMaps maps) {
+  using C = TileCfg<Real>;
+  using Acc = typename AccFor<Real>::type;
+  constexpr int V = C::V;
+  constexpr int KT = C::KT, KK = C::KK, K = C::K;
+  constexpr bool FORM = LANCZOS && FIRST;  // v_j is formed from (u_{j-1}, v_{j-1})
+
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ __align__(8) uint64_t full[kStages], empty[kStages], formed[kStages];
+  __shared__ double s_w[kStages][kMaxAtoms];  // w_q of the staged tile (first pass)
+  __shared__ double s_ehi[kStages];
+  __shared__ Coef s_cp[kMaxAtoms][2];         // [amplitude bit][bit of the target], apply form
+  __shared__ double s_red[3][kConsumerWarps];
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int n = args.n, L = args.L, c = args.c, a = args.a, f2 = args.f2;
+  const int nF2 = args.nF2, nG = args.nG, kt = args.kt, kk = L - V - kt;
+  const StepParams* sp = args.sp;
+  const int64_t num_tiles = args.num_tiles;
+  const uint32_t tile_bytes = (1u << L) * 2u * sizeof(Real);
+  const int64_t cmask = (int64_t(1) << c) - 1, f2mask = (int64_t(1) << nF2) - 1;
+
+  if (LANCZOS && args.ks->status != kContinue) return;  // uniform: Krylov space already accepted
+  const int jj = FORM ? args.ks->j : 0;
+  const bool has_prev = FORM && jj > 0;
+
+  if (tid == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], kConsumerWarps);
+      mbar_init(&formed[s], kConsumerWarps);
+    }
+    mbar_fence_init();
+  }
+  if (tid >= 32 && tid < 32 + n) {
+    const int q = tid - 32;
+    const double ho = sp->half_omega[q];
+    double sn = 0.0, cs = 1.0;
+    if (PHI) sincos(sp->phi[q], &sn, &cs);
+    // target bit 0: <0|h|1> = Omega/2 e^{+i phi}; target bit 1: <1|h|0> = Omega/2 e^{-i phi}
+    s_cp[q][0] = make_coef<Real, PHI>((Real)(ho * cs), (Real)(ho * sn));
+    s_cp[q][1] = make_coef<Real, PHI>((Real)(ho * cs), (Real)(-ho * sn));
+  }
+  Real* s_q = reinterpret_cast<Real*>(smem + (size_t)kStages * 2 * C::kTileBytes);
+  if (FIRST) {
+    const Real* qg = reinterpret_cast<const Real*>(args.qtab);
+    for (int i = tid; i < (1 << L); i += kConsumers) s_q[i] = qg[i];
+  }
+  __syncthreads();
+
+  auto stage_tile = [&](int s, int op) -> unsigned char* {
+    return smem + ((size_t)s * 2 + op) * C::kTileBytes;
+  };
+  auto tile_base = [&](int64_t tile) -> int64_t { return ((tile >> nF2) << c) | ((tile & f2mask) << f2); };
+
+  // ---- producer duties (warp 0): stream this CTA's tile number ip into stage
+  // ip % kStages with TMA; the next kStages - 1 tiles are always in flight ----
+  int produced = 0;
+  bool prod_ok = true;
+  auto produce = [&](int ip) {
+    const int64_t tile = blockIdx.x + (int64_t)ip * gridDim.x;
+    if (tile >= num_tiles || !prod_ok) return;
+    const int s = ip % kStages, r = ip / kStages;
+    if (ip >= kStages) {
+      // all warps released round r-1 of this stage
+      int ok = 1;
+      if (lane == 0) ok = mbar_wait(&empty[s], (r - 1) & 1) ? 1 : 0;
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      if (!ok) {
+        prod_ok = false;
+        if (lane == 0) atomicOr(args.err, 1);
+        return;
+      }
+    }
     if (FIRST) {
-      // Diagonal decomposition for this tile (c == L: tile bits == amplitude bits [0, L)).
-      if (tid < L) {
-        double w = -sp->delta[tid];
-        for (int r = L; r < n; ++r)
-          if ((tile >> (r - L)) & 1) w += args.vmat[tid * kMaxAtoms + r];
-        s_w[tid] = w;
+      // this tile's diagonal decomposition row (c == L: tile bits are amplitude bits [0, L))
+      if (lane < kDiagStride) {
+        const double v = args.diag[tile * kDiagStride + lane];
+        if (lane < L) s_w[s][lane] = v;
+        if (lane == kDiagStride - 1) s_ehi[s] = v;
       }
-      if (tid == 32) {
-        double e = 0.0;
-        for (int q = L; q < n; ++q) {
-          if (!((tile >> (q - L)) & 1)) continue;
-          e -= sp->delta[q];
-          for (int r = q + 1; r < n; ++r)
-            if ((tile >> (r - L)) & 1) e += args.vmat[q * kMaxAtoms + r];
-        }
-        s_ehi = e;
-      }
+      __syncwarp();
     }
-    // Load (or form) this thread's vectors and stage them in shared memory.
-    Real xr[K][R];
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      if (!active) continue;
-      const int tv = tid | (k << kt);
-      const int t = tv << V;
-      const int64_t amp = base | (t & cmask) | ((int64_t)(t >> c) << a);
-      const int64_t vidx = amp >> V;
-      if (LANCZOS && FIRST) {
-        Real u[R];
-        load_vec_cs<Real>(u, args.xin, vidx);
-        if (jj > 0) {
-          Real p[R];
-          load_vec<Real>(p, args.xprev, vidx);
-#pragma unroll
-          for (int i = 0; i < R; ++i) xr[k][i] = (u[i] - fa * p[i]) * fs;
-        } else {
-#pragma unroll
-          for (int i = 0; i < R; ++i) xr[k][i] = u[i] * fs;
-        }
-        store_vec<Real>(args.xout, vidx, xr[k]);
-      } else {
-        load_vec<Real>(xr[k], args.xin, vidx);
-      }
-#pragma unroll
-      for (int i = 0; i < R; ++i) sx[tv * R + i] = xr[k][i];
-    }
-    __syncthreads();
-    if (FIRST && tid < K) {
-      double s = 0.0;
-#pragma unroll
-      for (int jr = 0; jr < KK; ++jr)
-        if ((tid >> jr) & 1) s += s_w[V + kt + jr];
-      s_linreg[tid] = (Real)s;
-    }
-    Real lin_thread = 0;
-    if (FIRST) {
-      double s = s_ehi;
-      for (int j = 0; j < kt; ++j)
-        if ((tid >> j) & 1) s += s_w[V + j];
-      lin_thread = (Real)s;
-    }
-    if (FIRST) __syncthreads();  // s_linreg ready
-    if (!active) continue;
-
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      const int tv = tid | (k << kt);
-      const int t = tv << V;
-      const int64_t amp = base | (t & cmask) | ((int64_t)(t >> c) << a);
-      const int64_t vidx = amp >> V;
-      Real o[R];
+    if (lane == 0) {
       if (FIRST) {
-        const Real lk = lin_thread + s_linreg[k];
-#pragma unroll
-        for (int e = 0; e < NV; ++e) {
-          Real E = lk + qtab[t + e];
-          if (V == 1 && e == 1) E += (Real)s_w[0];
-          o[2 * e] = E * xr[k][2 * e];
-          o[2 * e + 1] = E * xr[k][2 * e + 1];
-        }
+        // contiguous tile: amplitude offset tile << L
+        const size_t off = (size_t)tile * tile_bytes;
+        mbar_arrive_expect_tx(&full[s], tile_bytes * (has_prev ? 2 : 1));
+        tma_load_1d(stage_tile(s, 0), static_cast<const unsigned char*>(args.xin) + off, tile_bytes, &full[s]);
+        if (has_prev)
+          tma_load_1d(stage_tile(s, 1), static_cast<const unsigned char*>(args.xprev) + off, tile_bytes, &full[s]);
       } else {
-        load_vec_cs<Real>(o, args.out, vidx);
+        const int c2 = (int)(tile >> nF2), c4 = (int)(tile & f2mask);
+        mbar_arrive_expect_tx(&full[s], tile_bytes * 2);
+        tma_load_5d(stage_tile(s, 0), &maps.x, 0, 0, c2, 0, c4, &full[s]);
+        tma_load_5d(stage_tile(s, 1), &maps.z, 0, 0, c2, 0, c4, &full[s]);
       }
-      // Tile bits [0, c) of the strided (second) pass are there only for
-      // coalescing: their flips belong to the first pass, so they are skipped.
-      // (a) vector-lane bit: tile bit 0 == amplitude bit 0 (requires c >= 1)
-      if (V == 1 && FIRST) {
-        cmac<Real, PHI>(o[0], o[1], s_coef[0][0][0], s_coef[0][0][1], xr[k][2], xr[k][3]);
-        cmac<Real, PHI>(o[2], o[3], s_coef[0][1][0], s_coef[0][1][1], xr[k][0], xr[k][1]);
+    }
+    __syncwarp();
+    produced = ip + 1;
+  };
+  if (warp == 0)
+    for (int ip = 0; ip < kStages - 1; ++ip) produce(ip);
+
+  {
+    // ---------------- consumers ----------------
+    const int ct = tid;
+    const bool active = ct < (1 << kt);
+    const int keff = 1 << kk;
+    // Without a phase a flip coefficient is the real Omega_q / 2 for both target
+    // bit states and lives in a register; with a phase it is read from s_cp.
+    unsigned long long cre_t[KT], cre_r[KK], cre_l = 0ull;
+    bool flip_t[KT], flip_r[KK];
+#pragma unroll
+    for (int j = 0; j < KT; ++j) {
+      const int tb = V + j;
+      flip_t[j] = j < kt && (FIRST || tb >= c);
+      cre_t[j] = flip_t[j] ? s_cp[tb < c ? tb : a + (tb - c)][0].rr : 0ull;
+    }
+#pragma unroll
+    for (int j = 0; j < KK; ++j) {
+      const int tb = V + kt + j;
+      flip_r[j] = j < kk && (FIRST || tb >= c);
+      cre_r[j] = flip_r[j] ? s_cp[tb < c ? tb : a + (tb - c)][0].rr : 0ull;
+    }
+    if (V == 1 && FIRST) cre_l = s_cp[0][0].rr;
+    auto coef_thread = [&](int j) -> Coef {
+      if (!PHI) return Coef{cre_t[j], 0ull};
+      const int tb = V + j;
+      return s_cp[tb < c ? tb : a + (tb - c)][(ct >> j) & 1];
+    };
+    auto coef_reg = [&](int j, int k) -> Coef {
+      if (!PHI) return Coef{cre_r[j], 0ull};
+      const int tb = V + kt + j;
+      return s_cp[tb < c ? tb : a + (tb - c)][(k >> j) & 1];
+    };
+    const Real fa = FORM ? (Real)args.ks->form_a : (Real)0;
+    const Real fs = FORM ? (Real)args.ks->form_s : (Real)1;
+    const Real bp = FORM ? (Real)args.ks->beta_prev : (Real)0;
+
+    Acc r0, r1, r2;
+    int i = 0;
+    for (int64_t tile = blockIdx.x; tile < num_tiles; tile += gridDim.x, ++i) {
+      if (warp == 0) produce(i + kStages - 1);
+      const int s = i % kStages, r = i / kStages;
+      if (!mbar_wait(&full[s], r & 1)) {
+        if (lane == 0) atomicOr(args.err, 1);
+        break;
       }
-      // (b) thread bits through shared memory
-      for (int j = FIRST ? 0 : (c > V ? c - V : 0); j < kt; ++j) {
-        const int tb = V + j;
-        const int q = tb < c ? tb : a + (tb - c);
-        const int bs = (tid >> j) & 1;
-        const Real cr = s_coef[q][bs][0], ci = s_coef[q][bs][1];
-        Real p[R];
-        *reinterpret_cast<typename CplxT<Real>::vec*>(p) =
-            *reinterpret_cast<const typename CplxT<Real>::vec*>(sx + (tv ^ (1 << j)) * R);
+      unsigned char* T0 = stage_tile(s, 0);
+      unsigned char* T1 = stage_tile(s, 1);
+      const int64_t base = tile_base(tile);
+      if (FORM) {
+        // v_j = (u_{j-1} - alpha_{j-1} v_{j-1}) / beta_j, in place, and into the basis
 #pragma unroll
-        for (int e = 0; e < NV; ++e) cmac<Real, PHI>(o[2 * e], o[2 * e + 1], cr, ci, p[2 * e], p[2 * e + 1]);
+        for (int k = 0; k < K; ++k) {
+          if (!active || k >= keff) continue;
+          const int tv = ct | (k << kt);
+          const Vec u = lds_vec(T0, tv);
+          const Vec v = has_prev ? lds_vec(T1, tv) : Vec{0ull, 0ull};
+          const Vec x = form<Real>(u, v, fa, fs, has_prev);
+          sts_vec(T0, tv, x);
+          const int t = tv << V;
+          const int64_t amp = base | (t & cmask) | ((int64_t)(t >> c) << a);
+          stg_vec(args.xout, amp >> V, x);
+        }
+        // every consumer's v_j is in shared memory before anyone reads partners
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&formed[s]);
+        if (!mbar_wait(&formed[s], r & 1)) {
+          if (lane == 0) atomicOr(args.err, 1);
+          break;
+        }
       }
-      // (c) register bits
+      Real lin = 0;
+      if (FIRST) {
+        double sacc = s_ehi[s];
 #pragma unroll
-      for (int jr = 0; jr < KK; ++jr) {
-        const int tb = V + kt + jr;
-        if (!FIRST && tb < c) continue;
-        const int q = tb < c ? tb : a + (tb - c);
-        const int bs = (k >> jr) & 1;
-        const Real cr = s_coef[q][bs][0], ci = s_coef[q][bs][1];
-#pragma unroll
-        for (int e = 0; e < NV; ++e)
-          cmac<Real, PHI>(o[2 * e], o[2 * e + 1], cr, ci, xr[k ^ (1 << jr)][2 * e], xr[k ^ (1 << jr)][2 * e + 1]);
+        for (int j = 0; j < KT; ++j)
+          if (j < kt && ((ct >> j) & 1)) sacc += s_w[s][V + j];
+        lin = (Real)sacc;
       }
-      // (d) G bits: partner tiles through L2
-      for (int g = 0; g < nG; ++g) {
-        const int q = f2 + g;
-        const int bs = (int)((tile >> g) & 1);
-        const Real cr = s_coef[q][bs][0], ci = s_coef[q][bs][1];
-        const int64_t pidx = vidx ^ (int64_t(1) << (q - V));
-        Real p[R];
-        if (LANCZOS && FIRST) {
-          Real u[R];
-          load_vec<Real>(u, args.xin, pidx);
-          if (jj > 0) {
-            Real pp[R];
-            load_vec<Real>(pp, args.xprev, pidx);
+      Vec o[K];
 #pragma unroll
-            for (int i = 0; i < R; ++i) p[i] = (u[i] - fa * pp[i]) * fs;
-          } else {
+      for (int k = 0; k < K; ++k) {
+        o[k] = Vec{0ull, 0ull};
+        if (!active || k >= keff) continue;
+        const int tv = ct | (k << kt);
+        const Vec x = lds_vec(T0, tv);
+        if (FIRST) {
+          Real lk = lin;
 #pragma unroll
-            for (int i = 0; i < R; ++i) p[i] = u[i] * fs;
+          for (int j = 0; j < KK; ++j)
+            if (j < kk && ((k >> j) & 1)) lk += (Real)s_w[s][V + kt + j];
+          const int t = tv << V;
+          const Real e0 = lk + s_q[t];
+          const Real e1 = V == 1 ? lk + (Real)s_w[s][0] + s_q[t + 1] : e0;
+          o[k] = scale2<Real>(x, e0, e1);
+          if constexpr (C::kF) {
+            // vector-lane bit: amplitude bit 0, the partner is the other half of the vector
+            cmac_word<PHI>(o[k].w0, PHI ? s_cp[0][0] : Coef{cre_l, 0ull}, x.w1);
+            cmac_word<PHI>(o[k].w1, PHI ? s_cp[0][1] : Coef{cre_l, 0ull}, x.w0);
           }
         } else {
-          load_vec<Real>(p, args.xin, pidx);
+          o[k] = lds_vec(T1, tv);
         }
 #pragma unroll
-        for (int e = 0; e < NV; ++e) cmac<Real, PHI>(o[2 * e], o[2 * e + 1], cr, ci, p[2 * e], p[2 * e + 1]);
-      }
-      // (e) three-term recurrence
-      if (LANCZOS && FIRST) {
-        if (jj > 0) {
-          Real p[R];
-          load_vec<Real>(p, args.xprev, vidx);
+        for (int j = 0; j < KT; ++j)
+          if (flip_t[j]) cmac<Real, PHI>(o[k], coef_thread(j), lds_vec(T0, tv ^ (1 << j)));
 #pragma unroll
-          for (int i = 0; i < R; ++i) o[i] = fma(-bp, p[i], o[i]);
+        for (int j = 0; j < KK; ++j)
+          if (flip_r[j]) cmac<Real, PHI>(o[k], coef_reg(j, k), lds_vec(T0, tv ^ (1 << (kt + j))));
+        if (has_prev) axpy<Real>(o[k], -bp, lds_vec(T1, tv));
+      }
+      if (active) {
+        // G bits: partners in neighbouring tiles, read through L2, two bits at a
+        // time for all of this thread's vectors (8 loads in flight per thread)
+        for (int g0 = 0; g0 < nG; g0 += 2) {
+          Vec p[2][K];
+#pragma unroll
+          for (int g = 0; g < 2; ++g) {
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+              p[g][k] = Vec{0ull, 0ull};
+              if (g0 + g >= nG || k >= keff) continue;
+              const int t = (ct | (k << kt)) << V;
+              const int64_t amp = base | (t & cmask) | ((int64_t)(t >> c) << a);
+              const int64_t pidx = (amp >> V) ^ (int64_t(1) << (f2 + g0 + g - V));
+              if (FORM) {
+                const Vec u = ldg_vec(args.xin, pidx);
+                const Vec v = has_prev ? ldg_vec(args.xprev, pidx) : Vec{0ull, 0ull};
+                p[g][k] = form<Real>(u, v, fa, fs, has_prev);
+              } else {
+                p[g][k] = ldg_vec(args.xin, pidx);
+              }
+            }
+          }
+#pragma unroll
+          for (int g = 0; g < 2; ++g) {
+            if (g0 + g >= nG) continue;
+            const Coef cg = s_cp[f2 + g0 + g][(tile >> (g0 + g)) & 1];
+#pragma unroll
+            for (int k = 0; k < K; ++k)
+              if (k < keff) cmac<Real, PHI>(o[k], cg, p[g][k]);
+          }
+        }
+        // store (and reduce)
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+          if (k >= keff) continue;
+          const int tv = ct | (k << kt);
+          const int t = tv << V;
+          const int64_t amp = base | (t & cmask) | ((int64_t)(t >> c) << a);
+          if (LANCZOS && LAST) reduce_vec<Real>(lds_vec(T0, tv), o[k], r0, r1, r2);
+          stg_vec(args.out, amp >> V, o[k]);
         }
       }
-      if (LANCZOS && LAST) {
+      // release the stage (generic writes to it must precede the next TMA write)
+      if (FORM) fence_proxy_async_smem();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[s]);
+    }
+    if (LANCZOS && LAST) {
+      Acc acc[3] = {r0, r1, r2};
 #pragma unroll
-        for (int i = 0; i < R; ++i) {
-          r0.dot(xr[k][i], o[i]);
-          r1.dot(o[i], o[i]);
-          r2.dot(xr[k][i], xr[k][i]);
-        }
+      for (int v = 0; v < 3; ++v) warp_merge(acc[v]);
+      if (lane == 0) {
+#pragma unroll
+        for (int v = 0; v < 3; ++v) s_red[v][warp] = acc[v].value();
       }
-      store_vec<Real>(args.out, vidx, o);
     }
   }
-  if (LANCZOS && LAST) {
-    Acc acc[3] = {r0, r1, r2};
-    __syncthreads();
-    block_reduce_write<3>(acc, s_red, args.partials + (int64_t)blockIdx.x * 3);
+  // On an aborted run, let copies still in flight into the ring land before the
+  // CTA exits (bounded); on a normal run these phases have already completed.
+  if (warp == 0 && lane == 0 && *args.err) {
+    for (int ip = produced - 1; ip >= 0 && ip >= produced - kStages; --ip)
+      mbar_wait(&full[ip % kStages], (ip / kStages) & 1);
+  }
+  // every thread of the CTA reaches this point: all waits above are bounded
+  __syncthreads();
+  if (LANCZOS && LAST && tid < 3) {
+    double sum = 0.0;
+    for (int w = 0; w < kConsumerWarps; ++w) sum += s_red[tid][w];
+    args.partials[(int64_t)blockIdx.x * 3 + tid] = sum;
   }
 }
 
 // ---------------------------------------------------------------------------
 // Host-side launch
 // ---------------------------------------------------------------------------
-
-template <typename Real, int KK, bool LANCZOS, bool FIRST, bool LAST, bool PHI>
-static cudaError_t launch_one(const TileArgs& args, int grid, cudaStream_t stream) {
-  auto fn = tile_kernel<Real, KK, LANCZOS, FIRST, LAST, PHI>;
-  const int smem = (1 << args.L) * 2 * (int)sizeof(Real);
-  static bool configured = false;  // per instantiation
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 1 << 16);
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
-  fn<<<grid, kThreads, smem, stream>>>(args);
-  return cudaGetLastError();
+template <typename Real>
+size_t tile_smem_bytes() {
+  return (size_t)kStages * 2 * TileCfg<Real>::kTileBytes + (sizeof(Real) << TileCfg<Real>::L);
 }
 
 template <typename Real, bool LANCZOS, bool FIRST, bool LAST, bool PHI>
-static cudaError_t dispatch_kk(const TileArgs& args, int kk, int grid, cudaStream_t stream) {
-  switch (kk) {
-    case 0: return launch_one<Real, 0, LANCZOS, FIRST, LAST, PHI>(args, grid, stream);
-    case 1: return launch_one<Real, 1, LANCZOS, FIRST, LAST, PHI>(args, grid, stream);
-    case 2: return launch_one<Real, 2, LANCZOS, FIRST, LAST, PHI>(args, grid, stream);
-    case 3: return launch_one<Real, 3, LANCZOS, FIRST, LAST, PHI>(args, grid, stream);
-    case 4: return launch_one<Real, 4, LANCZOS, FIRST, LAST, PHI>(args, grid, stream);
-    default: return cudaErrorInvalidValue;
+static cudaError_t launch_one(const TileArgs& args, const TileMaps* maps, int grid, cudaStream_t stream) {
+  auto fn = tile_kernel<Real, LANCZOS, FIRST, LAST, PHI>;
+  const size_t smem = tile_smem_bytes<Real>();
+  static bool configured = false;  // per instantiation
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    configured = true;
   }
+  static const TileMaps empty_maps{};
+  fn<<<grid, kTileThreads, smem, stream>>>(args, maps ? *maps : empty_maps);
+  return cudaGetLastError();
 }
 
 template <typename Real>
-static cudaError_t dispatch(const TileArgs& args, TileMode mode, bool phi, int grid, cudaStream_t stream) {
-  const int kk = args.L - Lanes<Real>::kLogVec - args.kt;
+static cudaError_t dispatch(const TileArgs& args, const TileMaps* maps, TileMode mode, bool phi, int grid,
+                            cudaStream_t stream) {
   switch (mode) {
     case TileMode::kMatvecFirst:
-      return phi ? dispatch_kk<Real, false, true, false, true>(args, kk, grid, stream)
-                 : dispatch_kk<Real, false, true, false, false>(args, kk, grid, stream);
+      return phi ? launch_one<Real, false, true, false, true>(args, maps, grid, stream)
+                 : launch_one<Real, false, true, false, false>(args, maps, grid, stream);
     case TileMode::kMatvecSecond:
-      return phi ? launch_one<Real, 4, false, false, false, true>(args, grid, stream)
-                 : launch_one<Real, 4, false, false, false, false>(args, grid, stream);
+      return phi ? launch_one<Real, false, false, false, true>(args, maps, grid, stream)
+                 : launch_one<Real, false, false, false, false>(args, maps, grid, stream);
     case TileMode::kLanczosSingle:
-      return phi ? dispatch_kk<Real, true, true, true, true>(args, kk, grid, stream)
-                 : dispatch_kk<Real, true, true, true, false>(args, kk, grid, stream);
+      return phi ? launch_one<Real, true, true, true, true>(args, maps, grid, stream)
+                 : launch_one<Real, true, true, true, false>(args, maps, grid, stream);
     case TileMode::kLanczosFirst:
-      return phi ? launch_one<Real, 4, true, true, false, true>(args, grid, stream)
-                 : launch_one<Real, 4, true, true, false, false>(args, grid, stream);
+      return phi ? launch_one<Real, true, true, false, true>(args, maps, grid, stream)
+                 : launch_one<Real, true, true, false, false>(args, maps, grid, stream);
     case TileMode::kLanczosSecond:
-      return phi ? launch_one<Real, 4, true, false, true, true>(args, grid, stream)
-                 : launch_one<Real, 4, true, false, true, false>(args, grid, stream);
+      return phi ? launch_one<Real, true, false, true, true>(args, maps, grid, stream)
+                 : launch_one<Real, true, false, true, false>(args, maps, grid, stream);
   }
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_tile(const TileArgs& args, TileMode mode, bool c64, bool phi, int grid, cudaStream_t stream) {
+cudaError_t launch_tile(const TileArgs& args, const TileMaps* maps, TileMode mode, bool c64, bool phi, int grid,
+                        cudaStream_t stream) {
   if (grid <= 0) return cudaErrorInvalidValue;
-  return c64 ? dispatch<float>(args, mode, phi, grid, stream) : dispatch<double>(args, mode, phi, grid, stream);
+  return c64 ? dispatch<float>(args, maps, mode, phi, grid, stream)
+             : dispatch<double>(args, maps, mode, phi, grid, stream);
+}
+
+// ---------------------------------------------------------------------------
+// Tensor maps of the strided pass (driver entry point, no link-time libcuda).
+// ---------------------------------------------------------------------------
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+bool encode_tile_map(CUtensorMap* out, const void* base, const TileArgs& g, bool c64) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return false;
+  // 8-byte elements: one per complex64 amplitude, two per complex128 amplitude.
+  // Dimensions (innermost first): amplitude bits [0, c0), [c0, c), [c, a),
+  // [a, a+h), [a+h, n); the box takes the first, second and fourth whole, so the
+  // tile lands in shared memory in tile-local order. c0 keeps a box edge <= 256.
+  const int lepa = c64 ? 0 : 1;
+  const uint64_t ab = c64 ? 8 : 16;
+  const int h = g.L - g.c;
+  const int c0 = g.c < 8 - lepa ? g.c : 8 - lepa;
+  cuuint64_t dims[5] = {(cuuint64_t)1 << (c0 + lepa), (cuuint64_t)1 << (g.c - c0), (cuuint64_t)1 << (g.a - g.c),
+                        (cuuint64_t)1 << h, (cuuint64_t)1 << (g.n - g.a - h)};
+  cuuint64_t strides[4] = {(cuuint64_t)(ab << c0), (cuuint64_t)(ab << g.c), (cuuint64_t)(ab << g.a),
+                           (cuuint64_t)(ab << (g.a + h))};
+  cuuint32_t box[5] = {(cuuint32_t)1 << (c0 + lepa), (cuuint32_t)1 << (g.c - c0), 1, (cuuint32_t)1 << h, 1};
+  cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+  for (int i = 0; i < 5; ++i)
+    if (box[i] > 256) return false;
+  if ((reinterpret_cast<uintptr_t>(base) & 15) != 0) return false;
+  const CUresult r = fn(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 5, const_cast<void*>(base), dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
 }
 
 }  // namespace rsv
