@@ -378,7 +378,10 @@ __global__ void __launch_bounds__(kThreads) combine_kernel(const CombineArgs A) 
   __shared__ Real s_cr[kMaxKrylov], s_ci[kMaxKrylov];
   __shared__ const Real* s_basis[kMaxKrylov];
   __shared__ double s_red[(kMaxAtoms + 1) * (kThreads / 32)];
-  const int tid = threadIdx.x;
+  constexpr int kMaxHi = kMaxAtoms - (V + 8 + KKMAX);  // chunk-index bits
+  __shared__ double s_hi[kThreads / 32][kMaxHi];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (lane < kMaxHi) s_hi[warp][lane] = 0.0;
   const int n = A.n;
   int m = 0;
   if (A.combine) {
@@ -397,7 +400,10 @@ __global__ void __launch_bounds__(kThreads) combine_kernel(const CombineArgs A) 
   const bool active = tid < (1 << kt);
   const int64_t nchunks = A.dim >> T;
 
-  Acc tot, lane_acc, reg_acc[KKMAX], hi_acc[kMaxAtoms];
+  // Every |psi_b|^2 product is made exact (TwoProduct) and every sum is
+  // compensated; the per-thread accumulators stay in registers (compile-time
+  // indices), the chunk-index bits use per-warp shared accumulators.
+  Acc tot, lane_acc, reg_acc[KKMAX];
   for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
     Acc ct;
 #pragma unroll
@@ -408,16 +414,25 @@ __global__ void __launch_bounds__(kThreads) combine_kernel(const CombineArgs A) 
       if (A.combine) {
 #pragma unroll
         for (int i = 0; i < R; ++i) x[i] = 0;
-        for (int jb = 0; jb < m; ++jb) {
-          Real b[R];
-          *reinterpret_cast<vec*>(b) = __ldcs(reinterpret_cast<const vec*>(s_basis[jb]) + vidx);
-          const Real cr = s_cr[jb], ci = s_ci[jb];
+        // basis vectors four at a time: the four loads are issued before their FMAs
+        for (int jb0 = 0; jb0 < m; jb0 += 4) {
+          Real b[4][R];
 #pragma unroll
-          for (int e = 0; e < NV; ++e) {
-            x[2 * e] = fma(cr, b[2 * e], x[2 * e]);
-            x[2 * e] = fma(-ci, b[2 * e + 1], x[2 * e]);
-            x[2 * e + 1] = fma(cr, b[2 * e + 1], x[2 * e + 1]);
-            x[2 * e + 1] = fma(ci, b[2 * e], x[2 * e + 1]);
+          for (int u = 0; u < 4; ++u) {
+            if (jb0 + u < m)
+              *reinterpret_cast<vec*>(b[u]) = __ldcs(reinterpret_cast<const vec*>(s_basis[jb0 + u]) + vidx);
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            if (jb0 + u >= m) continue;
+            const Real cr = s_cr[jb0 + u], ci = s_ci[jb0 + u];
+#pragma unroll
+            for (int e = 0; e < NV; ++e) {
+              x[2 * e] = fma(cr, b[u][2 * e], x[2 * e]);
+              x[2 * e] = fma(-ci, b[u][2 * e + 1], x[2 * e]);
+              x[2 * e + 1] = fma(cr, b[u][2 * e + 1], x[2 * e + 1]);
+              x[2 * e + 1] = fma(ci, b[u][2 * e], x[2 * e + 1]);
+            }
           }
         }
         reinterpret_cast<vec*>(A.psi)[vidx] = *reinterpret_cast<const vec*>(x);
@@ -439,9 +454,13 @@ __global__ void __launch_bounds__(kThreads) combine_kernel(const CombineArgs A) 
         if (jr < kk && ((k >> jr) & 1)) reg_acc[jr].merge_acc(pv);
     }
     tot.merge_acc(ct);
-    for (int q = T; q < n; ++q)
-      if ((ch >> (q - T)) & 1) hi_acc[q - T].merge_acc(ct);
+    // chunk-index bits: the warp's chunk total goes, by lane hq, into that warp's
+    // shared accumulator for chunk bit hq (FP64)
+    Acc cw = ct;
+    warp_merge(cw);
+    if (lane < kMaxHi && T + lane < n && ((ch >> lane) & 1)) s_hi[warp][lane] += cw.value();
   }
+  __syncwarp();
   // per-bit contributions of this thread
   Acc out[kMaxAtoms + 1];
   out[0] = tot;
@@ -449,8 +468,14 @@ __global__ void __launch_bounds__(kThreads) combine_kernel(const CombineArgs A) 
     Acc v;
     if (q < V) v = lane_acc;
     else if (q < V + kt) { if ((tid >> (q - V)) & 1) v = tot; }
-    else if (q < T) v = reg_acc[q - V - kt];
-    else v = hi_acc[q - T];
+    else if (q < T) {
+#pragma unroll
+      for (int jr = 0; jr < KKMAX; ++jr)
+        if (jr == q - V - kt) v = reg_acc[jr];
+    }
+    else if (lane == 0) {
+      v.add_double(s_hi[warp][q - T]);
+    }
     out[1 + q] = v;
   }
   block_reduce_write<kMaxAtoms + 1>(out, s_red, A.partials + (int64_t)blockIdx.x * (n + 1), n + 1);

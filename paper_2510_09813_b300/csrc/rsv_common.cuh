@@ -108,6 +108,11 @@ struct AccF {
     lo = __fadd_rn(lo, olo);
   }
   __device__ __forceinline__ void merge_acc(const AccF& o) { merge(o.hi, o.lo); }
+  // adds a double as an unevaluated float pair (exact to ~2^-48 relative)
+  __device__ __forceinline__ void add_double(double d) {
+    const float h = (float)d;
+    merge(h, (float)(d - (double)h));
+  }
   __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
 };
 
@@ -116,6 +121,7 @@ struct AccD {
   __device__ __forceinline__ void add(double b) { v += b; }
   __device__ __forceinline__ void dot(double x, double y) { v = fma(x, y, v); }
   __device__ __forceinline__ void merge_acc(const AccD& o) { v += o.v; }
+  __device__ __forceinline__ void add_double(double d) { v += d; }
   __device__ __forceinline__ double value() const { return v; }
 };
 

@@ -183,7 +183,7 @@ __device__ __forceinline__ void reduce_vec(const Vec& x, const Vec& o, Acc& r0, 
 // ---------------------------------------------------------------------------
 // The streaming pass.
 // ---------------------------------------------------------------------------
-template <typename Real, bool LANCZOS, bool FIRST, bool LAST, bool PHI>
+template <typename Real, bool LANCZOS, bool FIRST, bool LAST, bool PHI, bool FULL>
 __global__ void __launch_bounds__(kTileThreads, 1)
     tile_kernel(const TileArgs args, const __grid_constant__ TileMaps maps) {
   using C = TileCfg<Real>;
@@ -194,14 +194,15 @@ __global__ void __launch_bounds__(kTileThreads, 1)
 
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ __align__(8) uint64_t full[kStages], empty[kStages], formed[kStages];
-  __shared__ double s_w[kStages][kMaxAtoms];  // w_q of the staged tile (first pass)
-  __shared__ double s_ehi[kStages];
+  __shared__ Real s_w[kStages][kMaxAtoms];  // w_q of the staged tile (first pass), working precision
+  __shared__ Real s_ehi[kStages];
   __shared__ Coef s_cp[kMaxAtoms][2];         // [amplitude bit][bit of the target], apply form
   __shared__ double s_red[3][kConsumerWarps];
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int n = args.n, L = args.L, c = args.c, a = args.a, f2 = args.f2;
-  const int nF2 = args.nF2, nG = args.nG, kt = args.kt, kk = L - V - kt;
+  // FULL: the standard tile layout, known at compile time (no per-vector guards)
+  const int nF2 = args.nF2, nG = args.nG, kt = FULL ? KT : args.kt, kk = FULL ? KK : L - V - kt;
   const StepParams* sp = args.sp;
   const int64_t num_tiles = args.num_tiles;
   const uint32_t tile_bytes = (1u << L) * 2u * sizeof(Real);
@@ -263,8 +264,8 @@ __global__ void __launch_bounds__(kTileThreads, 1)
       // this tile's diagonal decomposition row (c == L: tile bits are amplitude bits [0, L))
       if (lane < kDiagStride) {
         const double v = args.diag[tile * kDiagStride + lane];
-        if (lane < L) s_w[s][lane] = v;
-        if (lane == kDiagStride - 1) s_ehi[s] = v;
+        if (lane < L) s_w[s][lane] = (Real)v;
+        if (lane == kDiagStride - 1) s_ehi[s] = (Real)v;
       }
       __syncwarp();
     }
@@ -359,60 +360,82 @@ __global__ void __launch_bounds__(kTileThreads, 1)
           break;
         }
       }
-      Real lin = 0;
-      if (FIRST) {
-        double sacc = s_ehi[s];
+      if (active) {
+        // this thread's vectors: tile-local index, global vector index, value
+        int tvk[K];
+        int64_t vidx[K];
+        Vec x[K], o[K];
 #pragma unroll
-        for (int j = 0; j < KT; ++j)
-          if (j < kt && ((ct >> j) & 1)) sacc += s_w[s][V + j];
-        lin = (Real)sacc;
-      }
-      Vec o[K];
-#pragma unroll
-      for (int k = 0; k < K; ++k) {
-        o[k] = Vec{0ull, 0ull};
-        if (!active || k >= keff) continue;
-        const int tv = ct | (k << kt);
-        const Vec x = lds_vec(T0, tv);
+        for (int k = 0; k < K; ++k) {
+          tvk[k] = ct | (k << kt);
+          const int t = tvk[k] << V;
+          vidx[k] = (base | (t & cmask) | ((int64_t)(t >> c) << a)) >> V;
+          x[k] = k < keff ? lds_vec(T0, tvk[k]) : Vec{0ull, 0ull};
+        }
         if (FIRST) {
-          Real lk = lin;
+          Real sacc = s_ehi[s];
 #pragma unroll
-          for (int j = 0; j < KK; ++j)
-            if (j < kk && ((k >> j) & 1)) lk += (Real)s_w[s][V + kt + j];
-          const int t = tv << V;
-          const Real e0 = lk + s_q[t];
-          const Real e1 = V == 1 ? lk + (Real)s_w[s][0] + s_q[t + 1] : e0;
-          o[k] = scale2<Real>(x, e0, e1);
-          if constexpr (C::kF) {
-            // vector-lane bit: amplitude bit 0, the partner is the other half of the vector
-            cmac_word<PHI>(o[k].w0, PHI ? s_cp[0][0] : Coef{cre_l, 0ull}, x.w1);
-            cmac_word<PHI>(o[k].w1, PHI ? s_cp[0][1] : Coef{cre_l, 0ull}, x.w0);
+          for (int j = 0; j < KT; ++j)
+            if (j < kt && ((ct >> j) & 1)) sacc += s_w[s][V + j];
+          const Real lin = sacc;
+#pragma unroll
+          for (int k = 0; k < K; ++k) {
+            Real lk = lin;
+#pragma unroll
+            for (int j = 0; j < KK; ++j)
+              if (j < kk && ((k >> j) & 1)) lk += s_w[s][V + kt + j];
+            const int t = tvk[k] << V;
+            const Real e0 = lk + s_q[t];
+            const Real e1 = V == 1 ? lk + s_w[s][0] + s_q[t + 1] : e0;
+            o[k] = scale2<Real>(x[k], e0, e1);
+            if constexpr (C::kF) {
+              // vector-lane bit: amplitude bit 0, the partner is the other half of the vector
+              cmac_word<PHI>(o[k].w0, PHI ? s_cp[0][0] : Coef{cre_l, 0ull}, x[k].w1);
+              cmac_word<PHI>(o[k].w1, PHI ? s_cp[0][1] : Coef{cre_l, 0ull}, x[k].w0);
+            }
           }
         } else {
-          o[k] = lds_vec(T1, tv);
+#pragma unroll
+          for (int k = 0; k < K; ++k) o[k] = k < keff ? lds_vec(T1, tvk[k]) : Vec{0ull, 0ull};
         }
+        // thread bits, bit-major: the K partner loads of one bit are independent
 #pragma unroll
-        for (int j = 0; j < KT; ++j)
-          if (flip_t[j]) cmac<Real, PHI>(o[k], coef_thread(j), lds_vec(T0, tv ^ (1 << j)));
+        for (int j = 0; j < KT; ++j) {
+          if (!flip_t[j]) continue;
+          const Coef cf = coef_thread(j);
+          Vec pp[K];
 #pragma unroll
-        for (int j = 0; j < KK; ++j)
-          if (flip_r[j]) cmac<Real, PHI>(o[k], coef_reg(j, k), lds_vec(T0, tv ^ (1 << (kt + j))));
-        if (has_prev) axpy<Real>(o[k], -bp, lds_vec(T1, tv));
-      }
-      if (active) {
+          for (int k = 0; k < K; ++k) pp[k] = k < keff ? lds_vec(T0, tvk[k] ^ (1 << j)) : Vec{0ull, 0ull};
+#pragma unroll
+          for (int k = 0; k < K; ++k) cmac<Real, PHI>(o[k], cf, pp[k]);
+        }
+        // register bits: the partner is another of this thread's own vectors
+#pragma unroll
+        for (int j = 0; j < KK; ++j) {
+          if (!flip_r[j]) continue;
+#pragma unroll
+          for (int k = 0; k < K; ++k)
+            if (k < keff) cmac<Real, PHI>(o[k], coef_reg(j, k), x[k ^ (1 << j)]);
+        }
+        if (has_prev) {
+#pragma unroll
+          for (int k = 0; k < K; ++k)
+            if (k < keff) axpy<Real>(o[k], -bp, lds_vec(T1, tvk[k]));
+        }
         // G bits: partners in neighbouring tiles, read through L2, two bits at a
         // time for all of this thread's vectors (8 loads in flight per thread)
         for (int g0 = 0; g0 < nG; g0 += 2) {
           Vec p[2][K];
 #pragma unroll
           for (int g = 0; g < 2; ++g) {
+            // a G bit is fixed per tile, so the partner sits at a uniform offset
+            const int64_t gstep = int64_t(1) << (f2 + g0 + g - V);
+            const int64_t goff = ((tile >> (g0 + g)) & 1) ? -gstep : gstep;
 #pragma unroll
             for (int k = 0; k < K; ++k) {
               p[g][k] = Vec{0ull, 0ull};
               if (g0 + g >= nG || k >= keff) continue;
-              const int t = (ct | (k << kt)) << V;
-              const int64_t amp = base | (t & cmask) | ((int64_t)(t >> c) << a);
-              const int64_t pidx = (amp >> V) ^ (int64_t(1) << (f2 + g0 + g - V));
+              const int64_t pidx = vidx[k] + goff;
               if (FORM) {
                 const Vec u = ldg_vec(args.xin, pidx);
                 const Vec v = has_prev ? ldg_vec(args.xprev, pidx) : Vec{0ull, 0ull};
@@ -435,11 +458,8 @@ __global__ void __launch_bounds__(kTileThreads, 1)
 #pragma unroll
         for (int k = 0; k < K; ++k) {
           if (k >= keff) continue;
-          const int tv = ct | (k << kt);
-          const int t = tv << V;
-          const int64_t amp = base | (t & cmask) | ((int64_t)(t >> c) << a);
-          if (LANCZOS && LAST) reduce_vec<Real>(lds_vec(T0, tv), o[k], r0, r1, r2);
-          stg_vec(args.out, amp >> V, o[k]);
+          if (LANCZOS && LAST) reduce_vec<Real>(x[k], o[k], r0, r1, r2);
+          stg_vec(args.out, vidx[k], o[k]);
         }
       }
       // release the stage (generic writes to it must precede the next TMA write)
@@ -480,9 +500,9 @@ size_t tile_smem_bytes() {
   return (size_t)kStages * 2 * TileCfg<Real>::kTileBytes + (sizeof(Real) << TileCfg<Real>::L);
 }
 
-template <typename Real, bool LANCZOS, bool FIRST, bool LAST, bool PHI>
-static cudaError_t launch_one(const TileArgs& args, const TileMaps* maps, int grid, cudaStream_t stream) {
-  auto fn = tile_kernel<Real, LANCZOS, FIRST, LAST, PHI>;
+template <typename Real, bool LANCZOS, bool FIRST, bool LAST, bool PHI, bool FULL>
+static cudaError_t launch_full(const TileArgs& args, const TileMaps* maps, int grid, cudaStream_t stream) {
+  auto fn = tile_kernel<Real, LANCZOS, FIRST, LAST, PHI, FULL>;
   const size_t smem = tile_smem_bytes<Real>();
   static bool configured = false;  // per instantiation
   if (!configured) {
@@ -493,6 +513,15 @@ static cudaError_t launch_one(const TileArgs& args, const TileMaps* maps, int gr
   static const TileMaps empty_maps{};
   fn<<<grid, kTileThreads, smem, stream>>>(args, maps ? *maps : empty_maps);
   return cudaGetLastError();
+}
+
+
+
+template <typename Real, bool LANCZOS, bool FIRST, bool LAST, bool PHI>
+static cudaError_t launch_one(const TileArgs& args, const TileMaps* maps, int grid, cudaStream_t stream) {
+  const bool full = args.kt == TileCfg<Real>::KT && args.L == TileCfg<Real>::L;
+  return full ? launch_full<Real, LANCZOS, FIRST, LAST, PHI, true>(args, maps, grid, stream)
+              : launch_full<Real, LANCZOS, FIRST, LAST, PHI, false>(args, maps, grid, stream);
 }
 
 template <typename Real>

@@ -119,5 +119,29 @@ __device__ __forceinline__ unsigned long long f2_mul(unsigned long long a, unsig
   asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
   return d;
 }
+__device__ __forceinline__ unsigned long long f2_add(unsigned long long a, unsigned long long b) {
+  unsigned long long d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ unsigned long long f2_sub(unsigned long long a, unsigned long long b) {
+  unsigned long long d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+
+// Two compensated FP32 accumulators in one packed pair (Knuth's TwoSum on both
+// lanes at once): value = hi + lo per lane. The f32x2 arithmetic rounds each
+// lane exactly like its scalar counterpart and is never contracted.
+struct AccF2 {
+  unsigned long long hi = 0ull, lo = 0ull;
+  __device__ __forceinline__ void add(unsigned long long b) {
+    const unsigned long long s = f2_add(hi, b);
+    const unsigned long long bp = f2_sub(s, hi);
+    const unsigned long long e = f2_add(f2_sub(hi, f2_sub(s, bp)), f2_sub(b, bp));
+    hi = s;
+    lo = f2_add(lo, e);
+  }
+};
 
 }  // namespace rsv
