@@ -323,6 +323,8 @@ def ours(args):
                          "traffic": None if tr is None else tr * amps,
                          "algorithmic_bytes_per_launch": per_launch_bytes},
             "kernels": kernels,
+            "tile_shape": {"passes": st["tile_passes"], "segment_bits": st["segment_bits"],
+                           "l2_partner_bits": st["l2_partner_bits"], "tile_order_bits": st["tile_order_bits"]},
             "matvec": {"ms": round(mv_ms, 4), "algo_GBps": round(mv_gbs, 1), "frac_of_peak": round(mv_gbs / hbm, 4),
                        "algorithmic_bytes": 16 * amps, "passes": 2},
             "e2e": {"value": e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": round(h2d),

@@ -101,6 +101,10 @@ typedef struct {
   double max_error_estimate;  /* largest accepted a-posteriori Krylov error estimate */
   double seconds;             /* wall time of the solve on the host */
   int64_t kernel_launches;    /* library kernels launched so far */
+  int32_t tile_passes;        /* streaming passes per matvec (1 or 2) */
+  int32_t segment_bits;       /* strided pass: contiguous amplitude bits per segment (autotuned) */
+  int32_t l2_partner_bits;    /* strided pass: bits whose flip partners are read through L2 */
+  int32_t tile_order_bits;    /* strided pass: segment-index bits varied fastest across tiles (autotuned) */
 } rsv_stats;
 
 /* Kernel classes of the time step, for rsv_solver_kernel_times. */

@@ -26,6 +26,8 @@ struct TileArgs {
   int nF2;       // bits in the top fixed range (n - f2)
   int nG;        // lowest nG bits of the top range resolved by partner loads through L2 (<= 8)
   int kt;        // consumer-thread bits of the tile layout (<= 9)
+  int split_h;   // strided pass with L - c > 8: tensor-map layout that splits the strided range
+  int f1_fast;   // strided pass: segment-index bits varied fastest across tile numbers (0 = none)
   int64_t num_tiles;
   const StepParams* sp;  // device
   const double* vmat;    // device [kMaxAtoms][kMaxAtoms], FP64, by bit position

@@ -12,6 +12,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <set>
@@ -172,6 +173,8 @@ struct rsv_ctx {
   // open objects, freed by rsv_destroy if the caller did not free them first
   std::set<rsv_solver*> solvers;
   std::set<rsv_result*> results;
+  // autotuned contiguous-segment bits of the strided pass, per (n_atoms, complex64)
+  std::map<std::pair<int, int>, int> tuned_segment;
 };
 
 namespace {
@@ -186,7 +189,7 @@ struct Plan {
   int L_a = 0;         // tile bits of the first pass (Q table size)
 };
 
-Plan make_plan(int n, bool c64, int num_sms) {
+Plan make_plan(int n, bool c64, int num_sms, int seg_bits = kMinSegmentBits, int f1_fast = 0) {
   Plan p;
   const int lt = c64 ? kTileBitsC64 : kTileBitsC128;
   const int v = c64 ? 1 : 0;
@@ -207,9 +210,11 @@ Plan make_plan(int n, bool c64, int num_sms) {
     geom(p.a, lt, lt, lt, n - lt);
   } else {
     geom(p.a, lt, lt, lt, 0);
-    const int h = std::min(n - lt, lt - kMinSegmentBits);
+    const int h = std::min(n - lt, lt - seg_bits);
     const int c = lt - h;
     geom(p.b, lt, c, lt, 0);
+    p.b.split_h = (lt - c) > 8;
+    p.b.f1_fast = std::min(f1_fast, p.b.a - p.b.c);
     p.b.nG = p.b.nF2;  // callers check nG <= kMaxGBits
     p.two_pass = true;
   }
@@ -319,6 +324,72 @@ bool any_phi(const std::vector<StepParams>& sp, int n) {
     for (int q = 0; q < n; ++q)
       if (s.phi[q] != 0.0) return true;
   return false;
+}
+
+// Strided-pass shape autotuner. The contiguous segment of the strided tile
+// (2^c amplitudes) trades DRAM segment length against partner bits read through
+// L2, and the tile order (f1_fast segment-index bits varied fastest) trades DRAM
+// row locality against the L2 reuse distance of those partners. Candidates
+// c in {4, 5} x f1_fast in {0, 2, 4} are timed on the caller's buffers (the pass
+// only reads x and read-modify-writes z, whose contents do not matter here) and
+// the fastest is cached per (n_atoms, precision). RSV_SEGMENT_BITS fixes c.
+int segment_override() {
+  const char* e = std::getenv("RSV_SEGMENT_BITS");
+  if (!e) return 0;
+  const int v = std::atoi(e);
+  return (v >= 2 && v <= 8) ? v : 0;
+}
+
+// Tuned shape packed as seg_bits * 16 + f1_fast.
+int shape_for(rsv_ctx* ctx, int n, bool c64) {
+  if (const int o = segment_override()) return o * 16;
+  auto it = ctx->tuned_segment.find({n, c64 ? 1 : 0});
+  return it == ctx->tuned_segment.end() ? kMinSegmentBits * 16 : it->second;
+}
+
+int tune_shape(rsv_ctx* ctx, int n, bool c64, StepParams* sp, double* vmat, KState* ks, double* part, void* x,
+               void* z) {
+  if (const int o = segment_override()) return o * 16;
+  const auto key = std::make_pair(n, c64 ? 1 : 0);
+  auto it = ctx->tuned_segment.find(key);
+  if (it != ctx->tuned_segment.end()) return it->second;
+  int best = kMinSegmentBits * 16;
+  float best_ms = 1e30f;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  for (int cand = 0; cand < 6; ++cand) {
+    const int seg = cand < 3 ? 4 : 5, f1f = (cand % 3) * 2;
+    Plan p = make_plan(n, c64, ctx->num_sms, seg, f1f);
+    if (!p.two_pass || p.b.nG > kMaxGBits || p.b.c < (c64 ? 1 : 0)) continue;
+    TileArgs b = p.b;
+    b.sp = sp;
+    b.vmat = vmat;
+    b.ks = ks;
+    b.partials = part;
+    b.err = err_ptr(ks);
+    b.xin = x;
+    b.out = z;
+    TileMaps maps;
+    if (!encode_tile_map(&maps.x, x, p.b, c64) || !encode_tile_map(&maps.z, z, p.b, c64)) continue;
+    bool ok = launch_tile(b, &maps, TileMode::kMatvecSecond, c64, false, p.grid_b, ctx->stream) == cudaSuccess;
+    cudaEventRecord(e0, ctx->stream);
+    for (int r = 0; r < 3 && ok; ++r)
+      ok = launch_tile(b, &maps, TileMode::kMatvecSecond, c64, false, p.grid_b, ctx->stream) == cudaSuccess;
+    cudaEventRecord(e1, ctx->stream);
+    if (!ok || cudaEventSynchronize(e1) != cudaSuccess) continue;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = seg * 16 + f1f;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaMemsetAsync(err_ptr(ks), 0, sizeof(int), ctx->stream);
+  ctx->tuned_segment[key] = best;
+  return best;
 }
 
 // Launch one streaming pass.
@@ -745,7 +816,8 @@ rsv_status rsv_apply_hamiltonian(rsv_ctx* ctx, int32_t n_atoms, int32_t precisio
   }
   sp.has_phi = has_phi;
   const std::vector<double> vb = to_bit_matrix(n, v_pairs);
-  Plan plan = make_plan(n, c64, ctx->num_sms);
+  const int shape = shape_for(ctx, n, c64);
+  Plan plan = make_plan(n, c64, ctx->num_sms, shape / 16, shape % 16);
   RSV_CUDA(cudaMemcpyAsync(ctx->d_sp, &sp, sizeof(sp), cudaMemcpyHostToDevice, ctx->stream));
   RSV_CUDA(cudaMemcpyAsync(ctx->d_vmat, vb.data(), vb.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
   std::vector<float> qf;
@@ -923,7 +995,7 @@ rsv_status rsv_solver_create(rsv_ctx* ctx, const rsv_problem* problem, const rsv
   s->c64 = cfg.precision == RSV_C64;
   s->dim = int64_t(1) << n;
   s->cfg = cfg;
-  s->plan = make_plan(n, s->c64, ctx->num_sms);
+  s->plan = make_plan(n, s->c64, ctx->num_sms);  // strided-pass shape tuned below
   RSV_TRY(step_params(problem, cfg.dt_ns, s->h_sp));
   s->nsteps = (int)s->h_sp.size();
   s->phi = any_phi(s->h_sp, n);
@@ -958,6 +1030,8 @@ rsv_status rsv_solver_create(rsv_ctx* ctx, const rsv_problem* problem, const rsv
     return fail(RSV_ERR_CUDA, std::string("cudaMallocHost: ") + cudaGetErrorString(e));
   }
   if (s->plan.two_pass) {
+    const int shape = tune_shape(ctx, n, s->c64, s->d_sp, s->d_vmat, s->d_ks, s->d_part, s->basis[0], s->d_u[0]);
+    s->plan = make_plan(n, s->c64, ctx->num_sms, shape / 16, shape % 16);
     s->map_basis.resize(cfg.m_max);
     bool ok = true;
     for (int k = 0; k < cfg.m_max; ++k) ok = ok && encode_tile_map(&s->map_basis[k], s->basis[k], s->plan.b, s->c64);
@@ -1113,6 +1187,10 @@ rsv_status rsv_solver_kernel_times(const rsv_solver* s, rsv_kernel_times* out) {
 rsv_status rsv_solver_stats(const rsv_solver* s, rsv_stats* out) {
   if (!s || !out) return fail(RSV_ERR_INVALID_ARG, "NULL argument");
   *out = s->stats;
+  out->tile_passes = s->plan.two_pass ? 2 : 1;
+  out->segment_bits = s->plan.two_pass ? s->plan.b.c : s->plan.a.c;
+  out->l2_partner_bits = s->plan.two_pass ? s->plan.b.nG : s->plan.a.nG;
+  out->tile_order_bits = s->plan.two_pass ? s->plan.b.f1_fast : 0;
   return RSV_OK;
 }
 

@@ -239,7 +239,15 @@ __global__ void __launch_bounds__(kTileThreads, 1)
   auto stage_tile = [&](int s, int op) -> unsigned char* {
     return smem + ((size_t)s * 2 + op) * C::kTileBytes;
   };
-  auto tile_base = [&](int64_t tile) -> int64_t { return ((tile >> nF2) << c) | ((tile & f2mask) << f2); };
+  // Tile index -> fixed bits: the lowest f1f index bits are segment-index (F1)
+  // bits, then the nF2 top-range (F2) bits, then the remaining F1 bits. f1f > 0
+  // makes neighbouring CTAs read adjacent segments (DRAM row locality); F2
+  // neighbours, whose partners come through L2, stay 2^(f1f + g) tiles apart.
+  const int f1f = args.f1_fast;
+  const int64_t f1fmask = (int64_t(1) << f1f) - 1;
+  auto f2_of = [&](int64_t t) -> int64_t { return (t >> f1f) & f2mask; };
+  auto f1_of = [&](int64_t t) -> int64_t { return (t & f1fmask) | ((t >> (f1f + nF2)) << f1f); };
+  auto tile_base = [&](int64_t tile) -> int64_t { return (f1_of(tile) << c) | (f2_of(tile) << f2); };
 
   // ---- producer duties (warp 0): stream this CTA's tile number ip into stage
   // ip % kStages with TMA; the next kStages - 1 tiles are always in flight ----
@@ -278,10 +286,15 @@ __global__ void __launch_bounds__(kTileThreads, 1)
         if (has_prev)
           tma_load_1d(stage_tile(s, 1), static_cast<const unsigned char*>(args.xprev) + off, tile_bytes, &full[s]);
       } else {
-        const int c2 = (int)(tile >> nF2), c4 = (int)(tile & f2mask);
+        const int cf1 = (int)f1_of(tile), cf2 = (int)f2_of(tile);
         mbar_arrive_expect_tx(&full[s], tile_bytes * 2);
-        tma_load_5d(stage_tile(s, 0), &maps.x, 0, 0, c2, 0, c4, &full[s]);
-        tma_load_5d(stage_tile(s, 1), &maps.z, 0, 0, c2, 0, c4, &full[s]);
+        if (args.split_h) {
+          tma_load_5d(stage_tile(s, 0), &maps.x, 0, cf1, 0, 0, cf2, &full[s]);
+          tma_load_5d(stage_tile(s, 1), &maps.z, 0, cf1, 0, 0, cf2, &full[s]);
+        } else {
+          tma_load_5d(stage_tile(s, 0), &maps.x, 0, 0, cf1, 0, cf2, &full[s]);
+          tma_load_5d(stage_tile(s, 1), &maps.z, 0, 0, cf1, 0, cf2, &full[s]);
+        }
       }
     }
     __syncwarp();
@@ -338,6 +351,7 @@ __global__ void __launch_bounds__(kTileThreads, 1)
       unsigned char* T0 = stage_tile(s, 0);
       unsigned char* T1 = stage_tile(s, 1);
       const int64_t base = tile_base(tile);
+      const int64_t tf2 = f2_of(tile);
       if (FORM) {
         // v_j = (u_{j-1} - alpha_{j-1} v_{j-1}) / beta_j, in place, and into the basis
 #pragma unroll
@@ -424,13 +438,16 @@ __global__ void __launch_bounds__(kTileThreads, 1)
         }
         // G bits: partners in neighbouring tiles, read through L2, two bits at a
         // time for all of this thread's vectors (8 loads in flight per thread)
-        for (int g0 = 0; g0 < nG; g0 += 2) {
-          Vec p[2][K];
+        // (the strided pass re-reads x from shared memory for its reductions, so
+        // x's registers hold a third bit of partner loads instead)
+        constexpr int GB = FIRST ? 2 : 3;
+        for (int g0 = 0; g0 < nG; g0 += GB) {
+          Vec p[GB][K];
 #pragma unroll
-          for (int g = 0; g < 2; ++g) {
+          for (int g = 0; g < GB; ++g) {
             // a G bit is fixed per tile, so the partner sits at a uniform offset
             const int64_t gstep = int64_t(1) << (f2 + g0 + g - V);
-            const int64_t goff = ((tile >> (g0 + g)) & 1) ? -gstep : gstep;
+            const int64_t goff = ((tf2 >> (g0 + g)) & 1) ? -gstep : gstep;
 #pragma unroll
             for (int k = 0; k < K; ++k) {
               p[g][k] = Vec{0ull, 0ull};
@@ -446,9 +463,9 @@ __global__ void __launch_bounds__(kTileThreads, 1)
             }
           }
 #pragma unroll
-          for (int g = 0; g < 2; ++g) {
+          for (int g = 0; g < GB; ++g) {
             if (g0 + g >= nG) continue;
-            const Coef cg = s_cp[f2 + g0 + g][(tile >> (g0 + g)) & 1];
+            const Coef cg = s_cp[f2 + g0 + g][(tf2 >> (g0 + g)) & 1];
 #pragma unroll
             for (int k = 0; k < K; ++k)
               if (k < keff) cmac<Real, PHI>(o[k], cg, p[g][k]);
@@ -458,7 +475,7 @@ __global__ void __launch_bounds__(kTileThreads, 1)
 #pragma unroll
         for (int k = 0; k < K; ++k) {
           if (k >= keff) continue;
-          if (LANCZOS && LAST) reduce_vec<Real>(x[k], o[k], r0, r1, r2);
+          if (LANCZOS && LAST) reduce_vec<Real>(FIRST ? x[k] : lds_vec(T0, tvk[k]), o[k], r0, r1, r2);
           stg_vec(args.out, vidx[k], o[k]);
         }
       }
@@ -582,15 +599,33 @@ bool encode_tile_map(CUtensorMap* out, const void* base, const TileArgs& g, bool
   // Dimensions (innermost first): amplitude bits [0, c0), [c0, c), [c, a),
   // [a, a+h), [a+h, n); the box takes the first, second and fourth whole, so the
   // tile lands in shared memory in tile-local order. c0 keeps a box edge <= 256.
+  // When the strided range is wider than a box edge (h > 8), the contiguous
+  // segment is kept whole and the strided range is split instead (kernel side:
+  // TileArgs::split_h selects the matching coordinate order).
   const int lepa = c64 ? 0 : 1;
   const uint64_t ab = c64 ? 8 : 16;
   const int h = g.L - g.c;
-  const int c0 = g.c < 8 - lepa ? g.c : 8 - lepa;
-  cuuint64_t dims[5] = {(cuuint64_t)1 << (c0 + lepa), (cuuint64_t)1 << (g.c - c0), (cuuint64_t)1 << (g.a - g.c),
-                        (cuuint64_t)1 << h, (cuuint64_t)1 << (g.n - g.a - h)};
-  cuuint64_t strides[4] = {(cuuint64_t)(ab << c0), (cuuint64_t)(ab << g.c), (cuuint64_t)(ab << g.a),
-                           (cuuint64_t)(ab << (g.a + h))};
-  cuuint32_t box[5] = {(cuuint32_t)1 << (c0 + lepa), (cuuint32_t)1 << (g.c - c0), 1, (cuuint32_t)1 << h, 1};
+  cuuint64_t dims[5], strides[4];
+  cuuint32_t box[5];
+  if (!g.split_h) {
+    const int c0 = g.c < 8 - lepa ? g.c : 8 - lepa;
+    const cuuint64_t d[5] = {(cuuint64_t)1 << (c0 + lepa), (cuuint64_t)1 << (g.c - c0),
+                             (cuuint64_t)1 << (g.a - g.c), (cuuint64_t)1 << h, (cuuint64_t)1 << (g.n - g.a - h)};
+    const cuuint64_t st[4] = {(cuuint64_t)(ab << c0), (cuuint64_t)(ab << g.c), (cuuint64_t)(ab << g.a),
+                              (cuuint64_t)(ab << (g.a + h))};
+    const cuuint32_t b[5] = {(cuuint32_t)1 << (c0 + lepa), (cuuint32_t)1 << (g.c - c0), 1, (cuuint32_t)1 << h, 1};
+    for (int i = 0; i < 5; ++i) dims[i] = d[i], box[i] = b[i];
+    for (int i = 0; i < 4; ++i) strides[i] = st[i];
+  } else {
+    const int h0 = 8;
+    const cuuint64_t d[5] = {(cuuint64_t)1 << (g.c + lepa), (cuuint64_t)1 << (g.a - g.c), (cuuint64_t)1 << h0,
+                             (cuuint64_t)1 << (h - h0), (cuuint64_t)1 << (g.n - g.a - h)};
+    const cuuint64_t st[4] = {(cuuint64_t)(ab << g.c), (cuuint64_t)(ab << g.a), (cuuint64_t)(ab << (g.a + h0)),
+                              (cuuint64_t)(ab << (g.a + h))};
+    const cuuint32_t b[5] = {(cuuint32_t)1 << (g.c + lepa), 1, (cuuint32_t)1 << h0, (cuuint32_t)1 << (h - h0), 1};
+    for (int i = 0; i < 5; ++i) dims[i] = d[i], box[i] = b[i];
+    for (int i = 0; i < 4; ++i) strides[i] = st[i];
+  }
   cuuint32_t estr[5] = {1, 1, 1, 1, 1};
   for (int i = 0; i < 5; ++i)
     if (box[i] > 256) return false;
