@@ -6,7 +6,7 @@
  *
  *   H(t) = sum_i Omega_i(t)/2 (cos phi_i X_i - sin phi_i Y_i) - sum_i delta_i(t) n_i
  *          + sum_{i<j} C6 / |r_i - r_j|^6 n_i n_j                  (Eq. (3), plus a phase)
- *   psi_{k+1} = exp(-i H_k dt) psi_k                               (Eq. (5))
+ *   psi_{k+1} = exp(-i H_k dt) psi_k                               (Eq. (6))
  *
  * with H_k taken at the midpoint of step k from pulses sampled every 1 ns
  * (Sec. III) and exp(-i H_k dt) psi_k evaluated by Lanczos (Sec. III.A).
@@ -197,7 +197,7 @@ RSV_API rsv_status rsv_sample(rsv_ctx* ctx, int32_t n_atoms, int32_t precision, 
 RSV_API rsv_status rsv_solver_create(rsv_ctx* ctx, const rsv_problem* problem, const rsv_config* config, rsv_solver** out);
 RSV_API void rsv_solver_destroy(rsv_solver* s);
 /* Advances up to n_steps time steps (stops at the end of the sequence).
- * Each step is one Lanczos evaluation of exp(-i H_k dt) psi (Eq. (5)), split
+ * Each step is one Lanczos evaluation of exp(-i H_k dt) psi (Eq. (6)), split
  * into Krylov restarts when m_max is reached. Records <n_i> per obs_stride.
  * Returns after the last step's work is complete on the device. */
 RSV_API rsv_status rsv_solver_step(rsv_solver* s, int32_t n_steps);

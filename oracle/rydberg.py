@@ -14,7 +14,7 @@ What it computes (arXiv 2510.09813):
     and <0|h|1> = Omega/2 e^{+i phi}.
   * Basis order: row-major N-index tensor of Eq. (4) (Sec. II.B): atom 0 is the
     most significant bit, b = sum_i b_i 2^(N-1-i).
-  * Time discretisation, Sec. III and Eq. (5): pulses sampled at t_n = n ns, held
+  * Time discretisation, Sec. III and Eq. (6): pulses sampled at t_n = n ns, held
     constant over each step of dt ns at their midpoint value
     (s[floor(m)] + s[ceil(m)])/2 with m = (n + 1/2) dt; psi_{k+1} = exp(-i H_k dt) psi_k.
   * Lanczos (Krylov) evaluation of exp(-i H dt) psi (Sec. III.A), here with full
@@ -57,7 +57,7 @@ def pair_interactions(positions, c6: float) -> np.ndarray:
 
 
 # ---------------------------------------------------------------------------
-# Time discretisation (Sec. III, Eq. (5))
+# Time discretisation (Sec. III, Eq. (6))
 # ---------------------------------------------------------------------------
 
 
@@ -324,7 +324,7 @@ def occupations(psi: np.ndarray) -> np.ndarray:
 def evolve(positions, c6, t_ns, dt_ns, omega, delta, phi=None, psi0=None,
            method: str = "krylov", tol: float = 1e-13, m_max: int = 60,
            record_occupations: bool = True):
-    """psi_K = exp(-i H_{K-1} tau) ... exp(-i H_0 tau) psi_0 (Eq. (5)).
+    """psi_K = exp(-i H_{K-1} tau) ... exp(-i H_0 tau) psi_0 (Eq. (6)).
 
     method = "dense" (expm of the brute-force matrix, N <= 12) or "krylov".
     Returns (psi_K, occ) where occ[k] = <n_i> after k steps (row 0 = psi_0).

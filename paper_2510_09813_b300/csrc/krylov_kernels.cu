@@ -1,5 +1,5 @@
 // Device-side Krylov control for exp(-i H_k dt) psi (arXiv 2510.09813, Sec. III.A
-// and Eq. (5)): reduction of the streaming passes' partial sums into the
+// and Eq. (6)): reduction of the streaming passes' partial sums into the
 // Lanczos scalars alpha_j, beta_{j+1}; the small exponential exp(-i tau T_m) e_1
 // in FP64; the convergence test; the Krylov combine psi' = |psi| sum_k u_k v_k;
 // and the observables <n_i> fused into the combine.

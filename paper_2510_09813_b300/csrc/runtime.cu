@@ -4,7 +4,7 @@
 //     arXiv 2510.09813 Sec. III.A.1),
 //   - host preparation: FP64 pair energies (Eq. (3)), midpoint pulse
 //     parameters (Sec. III), bit-position tables for the kernels,
-//   - the Lanczos time-step driver (Sec. III.A, Eq. (5)) over the streaming
+//   - the Lanczos time-step driver (Sec. III.A, Eq. (6)) over the streaming
 //     tile kernels and the device-side Krylov control kernels.
 #include <cuda_runtime.h>
 
