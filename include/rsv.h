@@ -190,6 +190,36 @@ RSV_API rsv_status rsv_observe(rsv_ctx* ctx, int32_t n_atoms, int32_t precision,
 RSV_API rsv_status rsv_sample(rsv_ctx* ctx, int32_t n_atoms, int32_t precision, const void* psi_dev, int64_t shots,
                       uint64_t seed, uint64_t* out);
 
+/* rsv_observe without a context and without allocating. The paper has no
+ * counterpart: it is a service entry, not a step of the method.
+ *
+ * For callers that hold a device state but must not allocate: a monitor that
+ * inspects a running job's state without changing its device footprint (once
+ * the job's arena and a framework's caching allocator hold HBM, a new
+ * allocation can fail, and it would escape the arena's admission accounting),
+ * and host loops that may not block (this call only enqueues work; rsv_observe
+ * allocates a context and synchronises).
+ *
+ * Writes out_dev[0] = |psi|^2 and out_dev[1 + i] = <n_i> = sum_b |psi_b|^2 b_i
+ * (atom order), FP64, into the caller's device array of n_atoms + 1 doubles
+ * (8-byte aligned). psi_dev: device state of 2^n_atoms amplitudes in
+ * `precision`, 16-byte aligned, caller-owned, only read. Both must be on the
+ * calling thread's current device. Work is enqueued on cuda_stream
+ * (NULL = the legacy default stream) and the call returns without waiting.
+ *
+ * Scratch: a fixed device array inside the library, 256 KiB of partial sums
+ * plus one status block (264,448 bytes), one copy per device. No scratch word
+ * has to start at zero (each word read is written earlier in the same call).
+ * n_atoms above 31 is rejected with RSV_ERR_INVALID_ARG and a message naming
+ * the limit. The first call on each device does the set-up (looks up the
+ * array's device address and the SM count, with that device current; this can
+ * load the library's device code): make it before any stream capture. Calls
+ * that overlap on one device (other threads or streams, before the previous
+ * call's work has finished) share the array and race: order them on one
+ * stream or serialise them. */
+RSV_API rsv_status rsv_observe_static(int32_t n_atoms, int32_t precision, const void* psi_dev, double* out_dev,
+                                      void* cuda_stream);
+
 /* ---- solver: a problem resident on the device --------------------------------- */
 
 /* Prepares a problem: pair energies, per-step midpoint parameters, the Krylov

@@ -81,6 +81,7 @@ def lib():
             "rsv_apply_hamiltonian": (I32, [P, I32, I32, PD, PD, PD, PD, P, P]),
             "rsv_observe": (I32, [P, I32, I32, P, PD, PD]),
             "rsv_sample": (I32, [P, I32, I32, P, I64, U64, C.POINTER(C.c_uint64)]),
+            "rsv_observe_static": (I32, [I32, I32, P, P, P]),
             "rsv_solver_create": (I32, [P, C.POINTER(Problem_), C.POINTER(Config_), C.POINTER(P)]),
             "rsv_solver_destroy": (None, [P]),
             "rsv_solver_step": (I32, [P, I32]),

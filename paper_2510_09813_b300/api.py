@@ -130,6 +130,20 @@ def observe(ctx: Context, n_atoms: int, precision, psi):
     return norm2.value, occ
 
 
+def observe_static(n_atoms: int, precision, psi, out, stream=None):
+    """rsv_observe_static: out[0] = |psi|^2, out[1 + i] = <n_i>, written on the
+    device into the caller's float64 CUDA tensor `out` (n_atoms + 1 entries)
+    without a context or any allocation; enqueued on `stream` (default: the
+    current torch stream), returns without waiting."""
+    torch = _torch()
+    if not (out.is_cuda and out.dtype == torch.float64 and out.is_contiguous() and out.numel() >= n_atoms + 1):
+        raise ValueError(f"out must be a contiguous CUDA float64 tensor of at least {n_atoms + 1} entries")
+    s = torch.cuda.current_stream(psi.device) if stream is None else stream
+    with torch.cuda.device(psi.device):
+        check(L.lib().rsv_observe_static(int(n_atoms), precision_code(precision), _check_state(psi, n_atoms, precision),
+                                         C.c_void_p(out.data_ptr()), C.c_void_p(s.cuda_stream or CUDA_STREAM_LEGACY)))
+
+
 def sample(ctx: Context, n_atoms: int, precision, psi, shots: int, seed: int) -> np.ndarray:
     out = np.empty(int(shots), dtype=np.uint64)
     check(L.lib().rsv_sample(ctx.handle, int(n_atoms), precision_code(precision),

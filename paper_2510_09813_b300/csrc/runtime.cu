@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -1262,6 +1263,129 @@ void rsv_result_free(rsv_result* r) {
   }
   delete r->solver;  // owned by the result, not in the context's solver set
   delete r;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// rsv_observe_static: the observation reduction of rsv_observe (combine
+// kernel in observe mode, then the begin kernel's FP64 reduction) with its
+// scratch in a fixed device array of this library instead of context memory,
+// so the call allocates nothing.
+//
+// Scratch layout (one copy per device, as every __device__ variable):
+//   [0, kStaticKsBytes)         a KState; the begin kernel writes its norm2
+//   [kStaticKsBytes, ...)       partial sums, grid rows of n + 1 doubles
+// Every scratch word the call reads is written earlier in the same call, so
+// nothing has to start at zero. Two calls in flight at once on one device
+// share the array and race.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int kStaticMaxAtoms = 31;                 // a partial row is n + 1 <= 32 doubles
+constexpr int kStaticPartialDoubles = 1024 * 32;    // 256 KiB of partial rows
+constexpr size_t kStaticKsBytes = (sizeof(KState) + 255) / 256 * 256;
+constexpr size_t kStaticScratchBytes = kStaticKsBytes + sizeof(double) * kStaticPartialDoubles;
+constexpr int kStaticMaxDevices = 64;
+
+struct StaticSlot {
+  std::atomic<unsigned char*> ptr{nullptr};
+  int num_sms = 0;
+};
+StaticSlot g_static_slots[kStaticMaxDevices];
+std::mutex g_static_mu;
+
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_observe_scratch[kStaticScratchBytes];
+
+namespace {
+
+// Set-up, once per device, with that device current: the device address of
+// the scratch array and the SM count. The first call on a device does it.
+rsv_status static_scratch(int device, unsigned char** ptr, int* num_sms) {
+  StaticSlot& s = g_static_slots[device];
+  unsigned char* p = s.ptr.load(std::memory_order_acquire);
+  if (!p) {
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    p = s.ptr.load(std::memory_order_relaxed);
+    if (!p) {
+      int sms = 0;
+      RSV_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
+      void* q = nullptr;
+      RSV_CUDA(cudaGetSymbolAddress(&q, g_observe_scratch));
+      if (!q || (reinterpret_cast<uintptr_t>(q) & 255))
+        return fail(RSV_ERR_CUDA, "rsv_observe_static: scratch array missing or not 256-byte aligned");
+      s.num_sms = sms;
+      p = static_cast<unsigned char*>(q);
+      s.ptr.store(p, std::memory_order_release);
+    }
+  }
+  *ptr = p;
+  *num_sms = s.num_sms;
+  return RSV_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+rsv_status rsv_observe_static(int32_t n_atoms, int32_t precision, const void* psi_dev, double* out_dev,
+                              void* cuda_stream) {
+  g_last_error.clear();
+  if (!psi_dev || !out_dev) return fail(RSV_ERR_INVALID_ARG, "rsv_observe_static: NULL argument");
+  if (precision != RSV_C64 && precision != RSV_C128) return fail(RSV_ERR_INVALID_ARG, "rsv_observe_static: bad precision");
+  if (n_atoms < 1) return fail(RSV_ERR_INVALID_ARG, "rsv_observe_static: n_atoms must be >= 1");
+  if (n_atoms > kStaticMaxAtoms)
+    return fail(RSV_ERR_INVALID_ARG, "rsv_observe_static: n_atoms = " + std::to_string(n_atoms) +
+                                         " exceeds the static scratch limit of " + std::to_string(kStaticMaxAtoms) +
+                                         " atoms (partial rows of at most 32 doubles)");
+  if (reinterpret_cast<uintptr_t>(psi_dev) & 15)
+    return fail(RSV_ERR_INVALID_ARG, "rsv_observe_static: psi must be 16-byte aligned");
+  if (reinterpret_cast<uintptr_t>(out_dev) & 7)
+    return fail(RSV_ERR_INVALID_ARG, "rsv_observe_static: out must be 8-byte aligned");
+  int device = -1;
+  RSV_CUDA(cudaGetDevice(&device));
+  if (device < 0 || device >= kStaticMaxDevices)
+    return fail(RSV_ERR_INVALID_ARG, "rsv_observe_static: device index beyond " + std::to_string(kStaticMaxDevices - 1));
+  unsigned char* scratch = nullptr;
+  int sms = 0;
+  RSV_TRY(static_scratch(device, &scratch, &sms));
+  const bool c64 = precision == RSV_C64;
+  const int nv = n_atoms + 1;
+  // same grid as rsv_observe (chunks of 2^T amplitudes, up to 4 CTAs per SM),
+  // capped by the rows the array holds
+  const int T = std::min(n_atoms, (c64 ? 1 : 0) + 8 + 4);
+  const int64_t chunks = int64_t(1) << (n_atoms - T);
+  int grid = (int)std::min<int64_t>(chunks, 4 * (int64_t)std::max(sms, 1));
+  grid = std::min(grid, kStaticPartialDoubles / nv);
+  const size_t need = kStaticKsBytes + sizeof(double) * (size_t)grid * nv;
+  if (need > kStaticScratchBytes)
+    return fail(RSV_ERR_INVALID_ARG, "rsv_observe_static: needs " + std::to_string(need) +
+                                         " bytes of scratch, the static array holds " +
+                                         std::to_string(kStaticScratchBytes));
+  KState* ks = reinterpret_cast<KState*>(scratch);
+  double* part = reinterpret_cast<double*>(scratch + kStaticKsBytes);
+  cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+  CombineArgs ca{};
+  ca.n = n_atoms;
+  ca.dim = int64_t(1) << n_atoms;
+  ca.ks = ks;
+  ca.psi = const_cast<void*>(psi_dev);
+  ca.partials = part;
+  ca.combine = 0;
+  RSV_CUDA(launch_combine(ca, c64, grid, stream));
+  BeginArgs ba{};
+  ba.ks = ks;
+  ba.partials = part;
+  ba.nparts = grid;
+  ba.n = n_atoms;
+  ba.occ_out = out_dev + 1;
+  ba.reset_only = 1;
+  RSV_CUDA(launch_begin(ba, stream));
+  RSV_CUDA(cudaMemcpyAsync(out_dev, scratch + offsetof(KState, norm2), sizeof(double), cudaMemcpyDeviceToDevice,
+                           stream));
+  return RSV_OK;
 }
 
 }  // extern "C"
