@@ -40,6 +40,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 N_ATOMS = 28
+BATCH_M_MAX = -1  # Krylov depth autotuned on a sample of the registers
+SERVE_ARENA = 160 << 30
+SERVE_REQUESTS = 32
 TRANSIENT_STEPS = 5  # steps of the Krylov space growing from |0...0> (13-19 iterations)
 DT_NS = 5
 M_MAX = 20
@@ -195,6 +198,87 @@ def reference_arm(args):
 
 
 # ---------------------------------------------------------------------------
+# Batched and served solves
+# ---------------------------------------------------------------------------
+
+BATCH_WORKLOAD = ("512 registers, N ~ U{10..18}, random 2D positions (min spacing 5 um), 8-knot piecewise-linear "
+                  "Omega/delta, T = 1 us, dt = 10 ns, complex64 (FP64-class reductions), one persistent launch "
+                  "(captured CUDA graph)")
+SERVE_WORKLOAD = ("Poisson arrivals (200 req/s) of solves with N ~ U{12..26}, random registers, 8-knot pulses, "
+                  "T ~ U[0.5, 3] us, dt = 10 ns, complex64 or complex128 (1/2 each)")
+
+
+def batched_leg(api, W, device: int):
+    """The 512-register batch in one persistent launch, against the
+    one-solve-at-a-time complex128 path on a sample of the same registers."""
+    import torch
+    probs = W.batch_registers()
+    ctx = api.Context(device)
+    b = api.Batch(ctx, probs, 10, "c64", m_max=BATCH_M_MAX, obs_stride=0)
+    b.run()
+    secs = []
+    for _ in range(3):
+        b.run()
+        secs.append(b.stats()["seconds"])
+    st = b.stats()
+    b.close()
+    sec = statistics.median(secs)
+    sample = list(range(0, len(probs), 32))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in sample:
+        r = api.run(ctx, probs[i], 10, "c128", obs_stride=0)
+        r.close()
+    one_s = (time.perf_counter() - t0) * len(probs) / len(sample)
+    ctx.close()
+    return {"workload": BATCH_WORKLOAD, "m_max": st["krylov_dim_max"], "m_max_autotuned": BATCH_M_MAX < 0,
+            "solves_per_s": len(probs) / sec,
+            "seconds": sec, "steps_per_s": st["steps"] / sec, "krylov_iterations_per_s": st["krylov_iterations"] / sec,
+            "resident_ctas": st["tile_passes"],
+            "one_at_a_time_c128": {"solves_per_s": len(probs) / one_s,
+                                   "sample": f"{len(sample)} of the {len(probs)} registers solved one by one "
+                                             f"(rsv_run, complex128), scaled to all"},
+            "speedup_vs_one_at_a_time_c128": one_s / sec}
+
+
+def serving_leg(api, W, device: int, count: int):
+    """Replay the first `count` requests of the serving stream at their arrival
+    times: continuous batching (4 slots, mixed precision) and the plain
+    one-solve-at-a-time complex128 server (1 slot, FIFO)."""
+    reqs = W.serving_stream(seed=5, count=count)
+    ctx = api.Context(device, arena_bytes=SERVE_ARENA)
+
+    def replay(slots, force_c128):
+        srv = api.Server(ctx, slots=slots, max_bypass_s=-1 if slots == 1 else 0.0)
+        t0 = time.perf_counter()
+        tickets = []
+        for r in reqs:
+            d = r.arrival_s - (time.perf_counter() - t0)
+            if d > 0:
+                time.sleep(d)
+            tickets.append(srv.submit(r.problem, 10, "c128" if force_c128 else r.precision, obs_stride=0))
+        lat, waits, servs = [], [], []
+        for t in tickets:
+            res = srv.poll(t)
+            w, v = res.times()
+            lat.append(w + v)
+            waits.append(w)
+            servs.append(v)
+            res.close()
+        span = time.perf_counter() - t0
+        srv.close()
+        q = lambda a, p: float(np.percentile(np.asarray(a), p))
+        return {"solves_per_s": len(reqs) / span, "p50_s": q(lat, 50), "p99_s": q(lat, 99),
+                "wait_p50_s": q(waits, 50), "service_p50_s": q(servs, 50), "span_s": span}
+
+    mixed = replay(4, False)
+    fifo = replay(1, True)
+    ctx.close()
+    return {"workload": SERVE_WORKLOAD, "requests": count, "continuous_batching": {"slots": 4, **mixed},
+            "one_at_a_time_c128": {"slots": 1, **fifo}}
+
+
+# ---------------------------------------------------------------------------
 # Our arm
 # ---------------------------------------------------------------------------
 
@@ -286,25 +370,31 @@ def ours(args):
                           "ms_per_launch": round(d["ms"] / d["launches"], 4),
                           "algo_GBps": round(d["bytes"] / (d["ms"] / 1e3) / 1e9, 1) if d["ms"] > 0 else None}
 
-    # pure matvec y = H x (two streaming passes, 16 B/amplitude algorithmic)
+    # pure matvec y = H x of the same register and pulse: the prepared operator
+    # enqueues its two streaming passes only. Algorithmic bytes 16 B/amp (read
+    # x, write y); the passes move 40 B/amp (first: read x, write y; second:
+    # read x and y, write y).
     import torch as T
     x = T.empty(amps, dtype=T.complex64, device="cuda")
     x.real.normal_()
+    x.imag.normal_()
     y = T.empty_like(x)
     V = api.pair_energies(prob.positions, prob.c6)
-    om, de = prob.omega[:, 0], prob.delta[:, 0]
+    ham = api.Hamiltonian(ctx, N_ATOMS, "c64", V, prob.omega[:, 0], prob.delta[:, 0], None)
     for _ in range(3):
-        api.apply_hamiltonian(ctx, N_ATOMS, "c64", V, om, de, None, x, y)
-    torch.cuda.synchronize()
+        ham.apply(x, y)
+    ham.sync()
     reps = 10
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(reps):
-        api.apply_hamiltonian(ctx, N_ATOMS, "c64", V, om, de, None, x, y)
+        ham.apply(x, y)
     e1.record(stream)
-    torch.cuda.synchronize()
+    ham.sync()
     mv_ms = e0.elapsed_time(e1) / reps
     mv_gbs = 16 * amps / (mv_ms / 1e3) / 1e9
+    mv_pass_gbs = 40 * amps / (mv_ms / 1e3) / 1e9
+    ham.close()
     del x, y
 
     # end to end through the whole-solve ABI: the state after the warm-up steps
@@ -332,6 +422,9 @@ def ours(args):
     d2h = occ.nbytes / e2e_steps
     res.close()
     ctx2.close()
+
+    batched = None if args.no_batch else batched_leg(api, W, local)
+    serving = None if args.serve_requests <= 0 else serving_leg(api, W, local, args.serve_requests)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -362,12 +455,15 @@ def ours(args):
             "tile_shape": {"passes": st["tile_passes"], "segment_bits": st["segment_bits"],
                            "l2_partner_bits": st["l2_partner_bits"], "tile_order_bits": st["tile_order_bits"]},
             "matvec": {"ms": round(mv_ms, 4), "algo_GBps": round(mv_gbs, 1), "frac_of_peak": round(mv_gbs / hbm, 4),
-                       "algorithmic_bytes": 16 * amps, "passes": 2},
+                       "algorithmic_bytes": 16 * amps, "passes": 2, "pass_bytes": 40 * amps,
+                       "pass_GBps": round(mv_pass_gbs, 1), "pass_frac_of_peak": round(mv_pass_gbs / hbm, 4)},
             "e2e": {"value": e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": round(h2d),
                     "d2h_bytes_per_step": round(d2h)},
             "gpu_launches": launches,
             "clocks": clk,
             "cpu_baseline": cpu,
+            "batched": batched,
+            "serving": serving,
         }
         print(json.dumps(line))
     if ws > 1:
@@ -406,6 +502,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 512-register batched leg")
+    ap.add_argument("--serve-requests", type=int, default=SERVE_REQUESTS,
+                    help="requests of the serving leg (0 skips it)")
     ap.add_argument("--profile-case", type=int, default=0, metavar="N",
                     help="run the small ncu case at N atoms instead of the benchmark")
     args = ap.parse_args()

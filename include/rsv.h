@@ -60,6 +60,9 @@ typedef int32_t rsv_status;
 typedef struct rsv_ctx rsv_ctx;
 typedef struct rsv_solver rsv_solver;
 typedef struct rsv_result rsv_result;
+typedef struct rsv_batch rsv_batch;
+typedef struct rsv_server rsv_server;
+typedef struct rsv_hamiltonian rsv_hamiltonian;
 
 /* One emulation problem in the paper's terms (Sec. II.A, Sec. III). All
  * pointers are host pointers owned by the caller; the library copies what it
@@ -105,6 +108,7 @@ typedef struct {
   int32_t segment_bits;       /* strided pass: contiguous amplitude bits per segment (autotuned) */
   int32_t l2_partner_bits;    /* strided pass: bits whose flip partners are read through L2 */
   int32_t tile_order_bits;    /* strided pass: segment-index bits varied fastest across tiles (autotuned) */
+  int32_t krylov_dim_max;     /* Krylov dimension cap in use (m_max; autotuned for batches created with m_max < 0) */
 } rsv_stats;
 
 /* Kernel classes of the time step, for rsv_solver_kernel_times. */
@@ -175,6 +179,21 @@ RSV_API rsv_status rsv_midpoint_parameters(const rsv_problem* problem, int32_t d
 RSV_API rsv_status rsv_apply_hamiltonian(rsv_ctx* ctx, int32_t n_atoms, int32_t precision, const double* v_pairs,
                                  const double* omega, const double* delta, const double* phi, const void* x_dev,
                                  void* y_dev);
+
+/* A prepared Hamiltonian (Eq. (3), same arguments as rsv_apply_hamiltonian)
+ * for repeated products: the parameter tables and the per-tile diagonal rows
+ * are built once on the device (context arena). */
+RSV_API rsv_status rsv_hamiltonian_create(rsv_ctx* ctx, int32_t n_atoms, int32_t precision, const double* v_pairs,
+                                          const double* omega, const double* delta, const double* phi,
+                                          rsv_hamiltonian** out);
+/* y = H x on caller-owned device buffers (2^n_atoms amplitudes, 16-byte
+ * aligned, not overlapping). Only enqueues the streaming passes on the context
+ * stream; nothing is allocated or synchronised. */
+RSV_API rsv_status rsv_hamiltonian_apply(rsv_hamiltonian* h, const void* x_dev, void* y_dev);
+/* Waits for the operator's enqueued products; RSV_ERR_TIMEOUT if a kernel's
+ * bounded wait gave up. */
+RSV_API rsv_status rsv_hamiltonian_sync(rsv_hamiltonian* h);
+RSV_API void rsv_hamiltonian_destroy(rsv_hamiltonian* h);
 
 /* |psi|^2 and <n_i> = sum_b |psi_b|^2 b_i (atom order) of a device state,
  * accumulated to FP64; results copied to the host arrays (occ may be NULL).
@@ -272,7 +291,80 @@ RSV_API rsv_status rsv_result_occupations(const rsv_result* r, double* dst, int3
 /* Samples of the final state (see rsv_sample). */
 RSV_API rsv_status rsv_result_sample(const rsv_result* r, int64_t shots, uint64_t seed, uint64_t* out);
 RSV_API rsv_status rsv_result_stats(const rsv_result* r, rsv_stats* out);
+/* Served requests: seconds from submission to admission (wait) and from
+ * admission to completion (service). rsv_run results: wait 0, service = the
+ * solve's wall time. */
+RSV_API rsv_status rsv_result_times(const rsv_result* r, double* wait_s, double* service_s);
 RSV_API void rsv_result_free(rsv_result* r);
+
+/* ---- batch: many independent registers in one persistent launch --------------- */
+
+/* Prepares `count` independent problems (each its own register, pulses and
+ * optional initial state) for batched evolution with one shared config
+ * (config->m_max < 0: the Krylov depth is autotuned on a sample of the
+ * registers among 12..40, see rsv_stats.krylov_dim_max). Each
+ * register has at most 20 atoms. Device memory: the states, a copy of the
+ * initial states, the per-step parameters, and per resident CTA a Krylov
+ * workspace of (m_max + 1) * 2^(largest n_atoms) amplitudes; all from the
+ * context arena (RSV_ERR_OUT_OF_MEMORY beyond its cap). The launch is captured
+ * once into a CUDA graph on a stream the batch owns. */
+RSV_API rsv_status rsv_batch_create(rsv_ctx* ctx, const rsv_problem* problems, int32_t count, const rsv_config* config,
+                                    rsv_batch** out);
+/* Resets every state to its initial state and evolves all registers over their
+ * whole pulse sequences (Eq. (6) per register, Sec. III.A) in one persistent
+ * kernel launch (graph replay): each CTA takes registers largest-first from a
+ * device work counter and runs a register's every step, Lanczos iteration,
+ * convergence test and substep on the device. Ordered after the context
+ * stream's earlier work; returns when done. RSV_ERR_NOT_CONVERGED if a
+ * register needed more than max_substeps substeps in a step. */
+RSV_API rsv_status rsv_batch_run(rsv_batch* b);
+/* Final state of register `index` (2^n amplitudes in the batch precision). */
+RSV_API rsv_status rsv_batch_state(const rsv_batch* b, int32_t index, void* host_dst, size_t bytes);
+/* Borrowed device pointer to that state, valid until rsv_batch_destroy. */
+RSV_API rsv_status rsv_batch_state_device(const rsv_batch* b, int32_t index, void** dev_ptr, size_t* bytes);
+/* Occupation rows [rows][n_atoms] of register `index`: t = 0, every obs_stride
+ * steps, and the end (as rsv_solver_occupations); dst NULL queries *n_rows. */
+RSV_API rsv_status rsv_batch_occupations(const rsv_batch* b, int32_t index, double* dst, int32_t capacity_rows,
+                                         int32_t* n_rows);
+/* Statistics of register `index`, or of the whole batch for index = -1
+ * (seconds = device time of the last run, kernel_launches = runs so far,
+ * tile_passes = resident CTAs of the launch). */
+RSV_API rsv_status rsv_batch_stats(const rsv_batch* b, int32_t index, rsv_stats* out);
+RSV_API void rsv_batch_destroy(rsv_batch* b);
+
+/* ---- serving: continuous admission of solves by device-memory footprint ------- */
+
+typedef struct {
+  int32_t slots;        /* solves in flight at once, each on its own CUDA stream; default 4 */
+  int32_t reserved;     /* must be 0 */
+  size_t memory_bytes;  /* device bytes admitted solves may hold together. 0: the context arena's
+                           free bytes at creation (capped context), else 90% of the device's free
+                           memory */
+  double max_bypass_s;  /* a queued request that does not fit may be passed by later requests that
+                           do only while it has waited less than this; 0 = default 0.5 s,
+                           negative = strict arrival order */
+} rsv_server_config;
+
+/* Starts a request server on a context. Worker threads take queued requests
+ * in arrival order whenever the request's device footprint (state, Krylov
+ * basis, work vectors, tables: the bytes its solver allocates) fits next to
+ * the solves already running, so requests arriving while others run are
+ * admitted as slots and memory free up, and their work overlaps on the device.
+ * A capped context arena is recommended: its allocations need no device-wide
+ * synchronisation. */
+RSV_API rsv_status rsv_server_create(rsv_ctx* ctx, const rsv_server_config* config, rsv_server** out);
+/* Queues one solve (the problem and config are copied; the call does not
+ * wait). RSV_ERR_OUT_OF_MEMORY if its footprint exceeds the server's memory. */
+RSV_API rsv_status rsv_submit(rsv_server* srv, const rsv_problem* problem, const rsv_config* config, uint64_t* ticket);
+/* Waits up to timeout_ms (negative: no limit; 0: just check) for a ticket.
+ * RSV_OK with *out = its result (the caller frees it; the ticket is then
+ * retired), RSV_ERR_TIMEOUT if still queued or running, RSV_ERR_NOT_FOUND for
+ * an unknown or retired ticket, or the solve's own error code. */
+RSV_API rsv_status rsv_poll(rsv_server* srv, uint64_t ticket, int32_t timeout_ms, rsv_result** out);
+/* Current load: queued and running requests, device bytes held by running ones. */
+RSV_API rsv_status rsv_server_load(rsv_server* srv, int32_t* queued, int32_t* running, size_t* bytes_in_use);
+/* Cancels queued requests, waits for running ones, frees unclaimed results. */
+RSV_API void rsv_server_destroy(rsv_server* srv);
 
 #ifdef __cplusplus
 }

@@ -47,10 +47,15 @@ class Stats_(C.Structure):
     _fields_ = [("steps", C.c_int64), ("krylov_iterations", C.c_int64), ("substeps", C.c_int64),
                 ("max_error_estimate", C.c_double), ("seconds", C.c_double), ("kernel_launches", C.c_int64),
                 ("tile_passes", C.c_int32), ("segment_bits", C.c_int32), ("l2_partner_bits", C.c_int32),
-                ("tile_order_bits", C.c_int32)]
+                ("tile_order_bits", C.c_int32), ("krylov_dim_max", C.c_int32)]
 
 
 KERNEL_KINDS = ("pass_first", "pass_second", "control", "combine")
+
+
+class ServerConfig_(C.Structure):
+    _fields_ = [("slots", C.c_int32), ("reserved", C.c_int32), ("memory_bytes", C.c_size_t),
+                ("max_bypass_s", C.c_double)]
 
 
 class KernelTimes_(C.Structure):
@@ -80,6 +85,10 @@ def lib():
             "rsv_midpoint_parameters": (I32, [C.POINTER(Problem_), I32, PD, PD, PD, PD]),
             "rsv_apply_hamiltonian": (I32, [P, I32, I32, PD, PD, PD, PD, P, P]),
             "rsv_observe": (I32, [P, I32, I32, P, PD, PD]),
+            "rsv_hamiltonian_create": (I32, [P, I32, I32, PD, PD, PD, PD, C.POINTER(P)]),
+            "rsv_hamiltonian_apply": (I32, [P, P, P]),
+            "rsv_hamiltonian_sync": (I32, [P]),
+            "rsv_hamiltonian_destroy": (None, [P]),
             "rsv_sample": (I32, [P, I32, I32, P, I64, U64, C.POINTER(C.c_uint64)]),
             "rsv_observe_static": (I32, [I32, I32, P, P, P]),
             "rsv_solver_create": (I32, [P, C.POINTER(Problem_), C.POINTER(Config_), C.POINTER(P)]),
@@ -102,6 +111,19 @@ def lib():
             "rsv_result_sample": (I32, [P, I64, U64, C.POINTER(C.c_uint64)]),
             "rsv_result_stats": (I32, [P, C.POINTER(Stats_)]),
             "rsv_result_free": (None, [P]),
+            "rsv_batch_create": (I32, [P, C.POINTER(Problem_), I32, C.POINTER(Config_), C.POINTER(P)]),
+            "rsv_batch_run": (I32, [P]),
+            "rsv_batch_state": (I32, [P, I32, P, SZ]),
+            "rsv_batch_state_device": (I32, [P, I32, C.POINTER(P), C.POINTER(SZ)]),
+            "rsv_batch_occupations": (I32, [P, I32, PD, I32, C.POINTER(I32)]),
+            "rsv_batch_stats": (I32, [P, I32, C.POINTER(Stats_)]),
+            "rsv_batch_destroy": (None, [P]),
+            "rsv_result_times": (I32, [P, PD, PD]),
+            "rsv_server_create": (I32, [P, C.POINTER(ServerConfig_), C.POINTER(P)]),
+            "rsv_submit": (I32, [P, C.POINTER(Problem_), C.POINTER(Config_), C.POINTER(U64)]),
+            "rsv_poll": (I32, [P, U64, I32, C.POINTER(P)]),
+            "rsv_server_load": (I32, [P, C.POINTER(I32), C.POINTER(I32), C.POINTER(SZ)]),
+            "rsv_server_destroy": (None, [P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)

@@ -121,6 +121,41 @@ def apply_hamiltonian(ctx: Context, n_atoms: int, precision, v_pairs, omega, del
         _check_state(x, n_atoms, precision), _check_state(y, n_atoms, precision)))
 
 
+class Hamiltonian:
+    """rsv_hamiltonian: H of Eq. (3) prepared once for repeated y = H x."""
+
+    def __init__(self, ctx: Context, n_atoms: int, precision, v_pairs, omega, delta, phi=None):
+        self.ctx, self.n, self.precision = ctx, int(n_atoms), precision_code(precision)
+        V = np.ascontiguousarray(np.asarray(v_pairs, dtype=np.float64))
+        om = np.ascontiguousarray(np.asarray(omega, dtype=np.float64))
+        de = np.ascontiguousarray(np.asarray(delta, dtype=np.float64))
+        ph = None if phi is None else np.ascontiguousarray(np.asarray(phi, dtype=np.float64))
+        self._h = C.c_void_p()
+        check(L.lib().rsv_hamiltonian_create(ctx.handle, self.n, self.precision, L._dptr(V), L._dptr(om), L._dptr(de),
+                                             L._dptr(ph) if ph is not None else C.POINTER(C.c_double)(),
+                                             C.byref(self._h)))
+        ctx._adopt(self)
+
+    def apply(self, x, y):
+        """Enqueue y = H x on the context stream (no synchronisation)."""
+        check(L.lib().rsv_hamiltonian_apply(self._h, _check_state(x, self.n, self.precision),
+                                            _check_state(y, self.n, self.precision)))
+
+    def sync(self):
+        check(L.lib().rsv_hamiltonian_sync(self._h))
+
+    def close(self):
+        if self._h:
+            L.lib().rsv_hamiltonian_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def observe(ctx: Context, n_atoms: int, precision, psi):
     """(|psi|^2, <n_i>[n]) of a CUDA state tensor."""
     norm2 = C.c_double()
@@ -270,9 +305,127 @@ class Result:
         check(L.lib().rsv_result_stats(self._h, C.byref(s)))
         return {k: getattr(s, k) for k, _ in L.Stats_._fields_}
 
+    def times(self) -> tuple[float, float]:
+        """(wait_s, service_s): queueing and solve time of a served request."""
+        w, v = C.c_double(), C.c_double()
+        check(L.lib().rsv_result_times(self._h, C.byref(w), C.byref(v)))
+        return w.value, v.value
+
     def close(self):
         if self._h:
             L.lib().rsv_result_free(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """rsv_batch: many independent registers (<= 20 atoms each) evolved over
+    their whole pulse sequences by one persistent launch (graph replay)."""
+
+    def __init__(self, ctx: Context, problems, dt_ns: int, precision="c64", krylov_tol=0.0, m_max=0,
+                 max_substeps=0, obs_stride=1, initial_states=None):
+        self.ctx = ctx
+        self.precision = precision_code(precision)
+        inits = initial_states if initial_states is not None else [None] * len(problems)
+        self._pas = []
+        for p, init in zip(problems, inits):
+            a = None if init is None else np.ascontiguousarray(np.asarray(init, dtype=amp_dtype(precision)))
+            self._pas.append(L.ProblemArgs.from_problem(p, a))
+        self.n = [pa.n for pa in self._pas]
+        arr = (L.Problem_ * len(self._pas))(*[pa.struct for pa in self._pas])
+        self._cfg = L.make_config(dt_ns, precision, krylov_tol, m_max, max_substeps, obs_stride)
+        self._h = C.c_void_p()
+        check(L.lib().rsv_batch_create(ctx.handle, arr, len(self._pas), C.byref(self._cfg), C.byref(self._h)))
+        ctx._adopt(self)
+
+    def __len__(self):
+        return len(self.n)
+
+    def run(self):
+        check(L.lib().rsv_batch_run(self._h))
+
+    def state(self, i: int) -> np.ndarray:
+        out = np.empty(2 ** self.n[i], dtype=amp_dtype(self.precision))
+        check(L.lib().rsv_batch_state(self._h, int(i), C.c_void_p(out.ctypes.data), out.nbytes))
+        return out
+
+    def state_device_ptr(self, i: int):
+        p, b = C.c_void_p(), C.c_size_t()
+        check(L.lib().rsv_batch_state_device(self._h, int(i), C.byref(p), C.byref(b)))
+        return p.value, b.value
+
+    def occupations(self, i: int) -> np.ndarray:
+        rows = C.c_int32()
+        check(L.lib().rsv_batch_occupations(self._h, int(i), C.POINTER(C.c_double)(), 0, C.byref(rows)))
+        out = np.empty((rows.value, self.n[i]))
+        check(L.lib().rsv_batch_occupations(self._h, int(i), L._dptr(out), rows.value, C.byref(rows)))
+        return out
+
+    def stats(self, i: int = -1) -> dict:
+        s = L.Stats_()
+        check(L.lib().rsv_batch_stats(self._h, int(i), C.byref(s)))
+        return {k: getattr(s, k) for k, _ in L.Stats_._fields_}
+
+    def close(self):
+        if self._h:
+            L.lib().rsv_batch_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """rsv_server: solves submitted at any time, admitted by device footprint,
+    run concurrently on their own streams (continuous batching)."""
+
+    def __init__(self, ctx: Context, slots: int = 4, memory_bytes: int = 0, max_bypass_s: float = 0.0):
+        self.ctx = ctx
+        cfg = L.ServerConfig_()
+        cfg.slots, cfg.reserved, cfg.memory_bytes, cfg.max_bypass_s = int(slots), 0, int(memory_bytes), float(max_bypass_s)
+        self._h = C.c_void_p()
+        check(L.lib().rsv_server_create(ctx.handle, C.byref(cfg), C.byref(self._h)))
+        self._precision = {}
+        ctx._adopt(self)
+
+    def submit(self, problem, dt_ns: int, precision="c64", krylov_tol=0.0, m_max=0, max_substeps=0, obs_stride=1,
+               initial_state=None) -> int:
+        init = None
+        if initial_state is not None:
+            init = np.ascontiguousarray(np.asarray(initial_state, dtype=amp_dtype(precision)))
+        pa = L.ProblemArgs.from_problem(problem, init)
+        cfg = L.make_config(dt_ns, precision, krylov_tol, m_max, max_substeps, obs_stride)
+        t = C.c_uint64()
+        check(L.lib().rsv_submit(self._h, C.byref(pa.struct), C.byref(cfg), C.byref(t)))
+        self._precision[t.value] = (pa.n, precision_code(precision))
+        return t.value
+
+    def poll(self, ticket: int, timeout_ms: int = -1):
+        """The Result of `ticket`, or None if it is still pending after timeout_ms."""
+        h = C.c_void_p()
+        code = L.lib().rsv_poll(self._h, C.c_uint64(ticket), int(timeout_ms), C.byref(h))
+        if code == -4:
+            return None
+        n, prec = self._precision.pop(ticket, (0, 0))
+        check(code)
+        return Result(self.ctx, h, n, prec)
+
+    def load(self) -> tuple[int, int, int]:
+        q, r, b = C.c_int32(), C.c_int32(), C.c_size_t()
+        check(L.lib().rsv_server_load(self._h, C.byref(q), C.byref(r), C.byref(b)))
+        return q.value, r.value, b.value
+
+    def close(self):
+        if self._h:
+            L.lib().rsv_server_destroy(self._h)
             self._h = C.c_void_p()
 
     def __del__(self):

@@ -103,6 +103,53 @@ struct CombineArgs {
 };
 cudaError_t launch_combine(const CombineArgs& a, bool c64, int grid, cudaStream_t stream);
 
+// Batched evolution of many small registers (batch_kernels.cu).
+constexpr int kBatchMaxAtoms = 20;
+
+struct BatchItem {       // one register, device descriptor
+  int32_t n;             // atoms
+  int32_t steps;         // time steps
+  int32_t obs_stride;    // occupation rows: t = 0, every obs_stride steps, and the end
+  int32_t has_phi;
+  int32_t occ_rows;      // capacity of the register's occupation rows
+  int32_t pad;
+  int64_t state_off;     // amplitudes into the state buffer
+  int64_t param_off;     // doubles into the step parameters: per step [tau, omega[n], delta[n], phi[n]] by bit position
+  int64_t vmat_off;      // doubles into the pair energies: [n][n] by bit position
+  int64_t occ_off;       // doubles into the occupation rows: [rows][n] by atom index
+};
+
+struct BatchOut {        // per-register result, written once by the CTA that ran it
+  int64_t iterations;
+  int64_t substeps;
+  double max_err;
+  double norm2;
+  int32_t status;        // 0, or RSV_ERR_NOT_CONVERGED
+  int32_t rows;          // occupation rows written
+};
+
+struct BatchArgs {
+  const BatchItem* items;
+  const int* order;      // processing order (largest registers first)
+  int count;
+  int* next;             // work counter, 0 at launch
+  void* states;
+  const double* params;
+  const double* vmat;
+  double* occ;
+  BatchOut* out;
+  void* work;            // per-CTA Krylov basis + work vector, work_stride amplitudes each
+  int64_t work_stride;
+  int m_max;
+  int max_substeps;
+  double tol;
+  double breakdown;
+};
+cudaError_t launch_batch(const BatchArgs& a, bool c64, int grid, cudaStream_t stream);
+// Sets the kernel's shared-memory attribute (call before launching or capturing)
+// and returns the resident CTAs per SM.
+int batch_prepare(bool c64);
+
 // Sampling (sample_kernels.cu)
 cudaError_t launch_block_sums(const void* psi, int64_t dim, bool c64, int64_t chunk, double* sums, cudaStream_t stream);
 cudaError_t launch_sample(const void* psi, int64_t dim, bool c64, int64_t chunk, const double* chunk_cdf, int64_t nchunks,

@@ -4,186 +4,10 @@
 // in FP64; the convergence test; the Krylov combine psi' = |psi| sum_k u_k v_k;
 // and the observables <n_i> fused into the combine.
 #include "kernels.h"
+#include "krylov_math.cuh"
 #include "rsv_common.cuh"
 
 namespace rsv {
-
-constexpr int kMaxBessel = 640;
-constexpr double kXMax = 400.0;  // largest Chebyshev argument per piece
-
-// ---------------------------------------------------------------------------
-// exp(-i tau T) w for a real symmetric tridiagonal T (m <= kMaxKrylov).
-//
-// Chebyshev expansion (Tal-Ezer & Kosloff, J. Chem. Phys. 81, 3967 (1984)):
-// with T = cen + rad * S, spec(S) in [-1, 1] by Gershgorin,
-//   exp(-i x S) = J_0(x) + 2 sum_{k>=1} (-i)^k J_k(x) T_k(S),   x = tau * rad,
-// (the Jacobi-Anger expansion) and T_k(S) w by the three-term recurrence.
-// J_k(x) comes from Miller's backward recurrence normalised by
-// J_0 + 2 sum_k J_{2k} = 1. Long times are split into pieces with x <= kXMax.
-// Called by one full warp; w lives in shared memory (re, im arrays).
-// ---------------------------------------------------------------------------
-__device__ void bessel_miller(double x, int K, double* J) {
-  // J[0..K] = J_k(x); computed by lane 0.
-  int M = K + 20 + (int)(5.0 * cbrt(x));
-  if (M > kMaxBessel - 2) M = kMaxBessel - 2;
-  double jp1 = 0.0, jk = 1e-280;
-  J[M] = jk;
-  for (int k = M; k >= 1; --k) {
-    const double jm1 = (2.0 * k / x) * jk - jp1;
-    J[k - 1] = jm1;
-    jp1 = jk;
-    jk = jm1;
-    if (fabs(jm1) > 1e250) {
-      for (int i = k - 1; i <= M; ++i) J[i] *= 1e-250;
-      jp1 *= 1e-250;
-      jk *= 1e-250;
-    }
-  }
-  double s = J[0];
-  for (int k = 2; k <= M; k += 2) s += 2.0 * J[k];
-  const double inv = 1.0 / s;
-  for (int k = 0; k <= K; ++k) J[k] *= inv;
-}
-
-struct ChebWork {
-  double pr[kMaxKrylov], pi[kMaxKrylov];  // phi_{k-1}
-  double cr[kMaxKrylov], ci[kMaxKrylov];  // phi_k
-  double ar[kMaxKrylov], ai[kMaxKrylov];  // accumulated sum
-  double J[kMaxBessel];
-  int kmax;
-};
-
-// Apply S = (T - cen)/rad to (vr, vi) component i.
-__device__ __forceinline__ void apply_s(const double* al, const double* be, int m, double cen, double irad, int i,
-                                        const double* vr, const double* vi, double& outr, double& outi) {
-  double r = (al[i] - cen) * vr[i], im = (al[i] - cen) * vi[i];
-  if (i > 0) {
-    r = fma(be[i], vr[i - 1], r);
-    im = fma(be[i], vi[i - 1], im);
-  }
-  if (i + 1 < m) {
-    r = fma(be[i + 1], vr[i + 1], r);
-    im = fma(be[i + 1], vi[i + 1], im);
-  }
-  outr = r * irad;
-  outi = im * irad;
-}
-
-__device__ __forceinline__ void acc_term(int k, double jk, double pr, double pi, double& ar, double& ai) {
-  // a_k = (2 - delta_k0) (-i)^k J_k
-  const double c = (k == 0) ? jk : 2.0 * jk;
-  switch (k & 3) {
-    case 0: ar = fma(c, pr, ar); ai = fma(c, pi, ai); break;
-    case 1: ar = fma(c, pi, ar); ai = fma(-c, pr, ai); break;
-    case 2: ar = fma(-c, pr, ar); ai = fma(-c, pi, ai); break;
-    default: ar = fma(-c, pi, ar); ai = fma(c, pr, ai); break;
-  }
-}
-
-// (ur, ui) <- exp(-i tau T_m) e_1.  al[0..m-1], be[1..m-1]; warp-collective.
-__device__ void cheb_expm_e1(const double* al, const double* be, int m, double tau, double* ur, double* ui,
-                             ChebWork& w) {
-  const int lane = threadIdx.x & 31;
-  double lo = 1e308, hi = -1e308;
-  for (int i = lane; i < m; i += 32) {
-    const double bl = i > 0 ? fabs(be[i]) : 0.0;
-    const double br = i + 1 < m ? fabs(be[i + 1]) : 0.0;
-    lo = fmin(lo, al[i] - bl - br);
-    hi = fmax(hi, al[i] + bl + br);
-  }
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
-    lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, off));
-    hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, off));
-  }
-  const double cen = 0.5 * (lo + hi), rad = 0.5 * (hi - lo);
-  for (int i = lane; i < m; i += 32) {
-    ur[i] = (i == 0) ? 1.0 : 0.0;
-    ui[i] = 0.0;
-  }
-  __syncwarp();
-  if (!(rad > 1e-300) || m == 1) {
-    if (lane == 0) {
-      double s, c;
-      sincos(tau * cen, &s, &c);
-      ur[0] = c;
-      ui[0] = -s;
-    }
-    __syncwarp();
-    return;
-  }
-  int pieces = (int)ceil(tau * rad / kXMax);
-  if (pieces < 1) pieces = 1;
-  const double tp = tau / pieces, x = tp * rad, irad = 1.0 / rad;
-  int K = (int)(x + 12.0 * cbrt(x) + 30.0);
-  if (K > kMaxBessel - 40) K = kMaxBessel - 40;
-  if (lane == 0) {
-    if (x < 1e-6) {
-      // power series J_k(x) = (x/2)^k / k! (1 - (x/2)^2 / (k+1) + ...), k <= 3
-      const double h = 0.5 * x;
-      w.J[0] = 1.0 - h * h;
-      w.J[1] = h * (1.0 - 0.5 * h * h);
-      w.J[2] = 0.5 * h * h;
-      w.J[3] = h * h * h / 6.0;
-      w.kmax = 3;
-    } else {
-      bessel_miller(x, K, w.J);
-      int kmax = K;
-      while (kmax > 1 && kmax > x && fabs(w.J[kmax]) < 1e-18) --kmax;
-      w.kmax = kmax;
-    }
-  }
-  __syncwarp();
-  const int kmax = w.kmax;
-  double ps, pc;
-  sincos(tp * cen, &ps, &pc);
-  for (int piece = 0; piece < pieces; ++piece) {
-    // phi_0 = u, phi_1 = S u
-    for (int i = lane; i < m; i += 32) {
-      w.pr[i] = ur[i];
-      w.pi[i] = ui[i];
-      w.ar[i] = 0.0;
-      w.ai[i] = 0.0;
-      acc_term(0, w.J[0], ur[i], ui[i], w.ar[i], w.ai[i]);
-    }
-    __syncwarp();
-    for (int i = lane; i < m; i += 32) {
-      double r, im;
-      apply_s(al, be, m, cen, irad, i, w.pr, w.pi, r, im);
-      w.cr[i] = r;
-      w.ci[i] = im;
-      acc_term(1, w.J[1], r, im, w.ar[i], w.ai[i]);
-    }
-    __syncwarp();
-    for (int k = 2; k <= kmax; ++k) {
-      double nr[2], ni[2];
-      int cnt = 0;
-      for (int i = lane; i < m; i += 32, ++cnt) {
-        double r, im;
-        apply_s(al, be, m, cen, irad, i, w.cr, w.ci, r, im);
-        nr[cnt] = 2.0 * r - w.pr[i];
-        ni[cnt] = 2.0 * im - w.pi[i];
-      }
-      __syncwarp();
-      cnt = 0;
-      for (int i = lane; i < m; i += 32, ++cnt) {
-        w.pr[i] = w.cr[i];
-        w.pi[i] = w.ci[i];
-        w.cr[i] = nr[cnt];
-        w.ci[i] = ni[cnt];
-        acc_term(k, w.J[k], nr[cnt], ni[cnt], w.ar[i], w.ai[i]);
-      }
-      __syncwarp();
-    }
-    // u = exp(-i tp cen) * acc
-    for (int i = lane; i < m; i += 32) {
-      const double r = w.ar[i], im = w.ai[i];
-      ur[i] = pc * r + ps * im;
-      ui[i] = pc * im - ps * r;
-    }
-    __syncwarp();
-  }
-}
 
 // ---------------------------------------------------------------------------
 // Scalar kernel: after the last streaming pass of Krylov iteration j.
@@ -223,51 +47,23 @@ __global__ void __launch_bounds__(kThreads) scalar_kernel(const ScalarArgs A) {
   const int m = j + 1;
   // alpha_j = Re<v_j, u_j> / |v_j|^2 and beta_{j+1} = |u_j - alpha_j v_j| expanded
   // as |u|^2 - 2 alpha Re<v,u> + alpha^2 |v|^2 = |u|^2 - alpha Re<v,u>.
-  const double alpha = r[0] / r[2];
-  const double b2 = r[1] - alpha * r[0];
-  const double beta = b2 > 0.0 ? sqrt(b2) : 0.0;
+  const LanczosScalars ls = lanczos_scalars(r[0], r[1], r[2]);
+  const double alpha = ls.alpha, beta = ls.beta;
+  const int mk = ls.vanished ? m - 1 : m;  // accepted dimension if this space ends here
   for (int i = lane; i < m; i += 32) s_al[i] = (i == j) ? alpha : ks->alpha[i];
   for (int i = lane; i <= m; i += 32) s_be[i] = (i == m) ? beta : ks->beta[i];
   __syncwarp();
   double tn = 0.0;
-  for (int i = lane; i < m; i += 32) tn = fmax(tn, fabs(s_al[i]) + fabs(s_be[i + 1]) + (i > 0 ? fabs(s_be[i]) : 0.0));
+  for (int i = lane; i < mk; i += 32) tn = fmax(tn, fabs(s_al[i]) + fabs(s_be[i + 1]) + (i > 0 ? fabs(s_be[i]) : 0.0));
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) tn = fmax(tn, __shfl_xor_sync(0xffffffffu, tn, off));
-  const bool breakdown = beta <= A.breakdown * fmax(tn, 1e-300);
+  const bool breakdown = ls.vanished || beta <= A.breakdown * fmax(tn, 1e-300);
   const bool check = breakdown || m >= A.check_from || m >= A.m_max;
-  int status = kContinue;
-  double tau_take = 0.0, err = 0.0;
+  const KrylovDecision d = krylov_decide(s_al, s_be, mk, ls.vanished ? 0.0 : beta, ks->tau_rem, breakdown, check,
+                                         A.m_max, A.tol, s_ur, s_ui, s_w);
+  const int status = d.status;
+  const double tau_take = d.tau_take, err = d.err;
   const double tau_rem = ks->tau_rem;
-  if (check) {
-    cheb_expm_e1(s_al, s_be, m, tau_rem, s_ur, s_ui, s_w);
-    err = beta * hypot(s_ur[m - 1], s_ui[m - 1]);
-    if (breakdown || err <= A.tol) {
-      status = kDone;
-      tau_take = tau_rem;
-    } else if (m >= A.m_max) {
-      // Largest t <= tau_rem whose estimate meets tol: halve until it does,
-      // then refine between t and 2t by bisection in log(t).
-      double t = tau_rem, t_bad = tau_rem;
-      for (int it = 0; it < 64; ++it) {
-        t_bad = t;
-        t *= 0.5;
-        cheb_expm_e1(s_al, s_be, m, t, s_ur, s_ui, s_w);
-        err = beta * hypot(s_ur[m - 1], s_ui[m - 1]);
-        if (err <= A.tol) break;
-      }
-      for (int it = 0; it < 4; ++it) {
-        const double tm = sqrt(t * t_bad);
-        cheb_expm_e1(s_al, s_be, m, tm, s_ur, s_ui, s_w);
-        const double em = beta * hypot(s_ur[m - 1], s_ui[m - 1]);
-        if (em <= A.tol) t = tm;
-        else t_bad = tm;
-      }
-      cheb_expm_e1(s_al, s_be, m, t, s_ur, s_ui, s_w);
-      err = beta * hypot(s_ur[m - 1], s_ui[m - 1]);
-      status = kDonePartial;
-      tau_take = t;
-    }
-  }
   if (lane == 0) {
     ks->alpha[j] = alpha;
     ks->beta[m] = beta;
@@ -275,14 +71,14 @@ __global__ void __launch_bounds__(kThreads) scalar_kernel(const ScalarArgs A) {
   }
   if (status != kContinue) {
     const double b0 = ks->beta[0];
-    for (int i = lane; i < m; i += 32) {
+    for (int i = lane; i < mk; i += 32) {
       ks->coef_re[i] = b0 * s_ur[i];
       ks->coef_im[i] = b0 * s_ui[i];
     }
     if (lane == 0) {
       double rem = tau_rem - tau_take;
       if (status == kDone || rem <= 1e-14 * tau_rem) rem = 0.0;
-      ks->m = m;
+      ks->m = mk;
       ks->tau_taken = tau_take;
       ks->tau_rem = rem;
       ks->err_est = err;

@@ -16,6 +16,10 @@
 #include <cstdlib>
 #include <cstring>
 #include <map>
+#include <thread>
+#include <deque>
+#include <condition_variable>
+#include <memory>
 #include <set>
 #include <mutex>
 #include <string>
@@ -174,6 +178,9 @@ struct rsv_ctx {
   // open objects, freed by rsv_destroy if the caller did not free them first
   std::set<rsv_solver*> solvers;
   std::set<rsv_result*> results;
+  std::set<rsv_batch*> batches;
+  std::set<rsv_server*> servers;
+  std::set<rsv_hamiltonian*> hamiltonians;
   // autotuned contiguous-segment bits of the strided pass, per (n_atoms, complex64)
   std::map<std::pair<int, int>, int> tuned_segment;
 };
@@ -320,6 +327,16 @@ rsv_status step_params(const rsv_problem* p, int dt_ns, std::vector<StepParams>&
   return RSV_OK;
 }
 
+// Device bytes a solver of this problem holds: rsv_footprint_bytes plus what
+// depends on the sequence (per-step parameters, recorded occupation rows).
+size_t solver_bytes(const rsv_problem* p, const rsv_config& cfg) {
+  const size_t steps = (size_t)num_steps(p->t_ns, cfg.dt_ns);
+  const size_t rows = (cfg.obs_stride > 0 ? steps / cfg.obs_stride : 0) + 2;
+  auto round = [](size_t b) { return (b + 255) & ~size_t(255); };
+  return rsv_footprint_bytes(p->n_atoms, cfg.precision, cfg.m_max) + round(sizeof(StepParams) * steps) +
+         round(sizeof(double) * p->n_atoms * rows);
+}
+
 bool any_phi(const std::vector<StepParams>& sp, int n) {
   for (const auto& s : sp)
     for (int q = 0; q < n; ++q)
@@ -348,7 +365,7 @@ int shape_for(rsv_ctx* ctx, int n, bool c64) {
   return it == ctx->tuned_segment.end() ? kMinSegmentBits * 16 : it->second;
 }
 
-int tune_shape(rsv_ctx* ctx, int n, bool c64, StepParams* sp, double* vmat, KState* ks, double* part, void* x,
+int tune_shape(rsv_ctx* ctx, cudaStream_t stream, int n, bool c64, StepParams* sp, double* vmat, KState* ks, double* part, void* x,
                void* z) {
   if (const int o = segment_override()) return o * 16;
   const auto key = std::make_pair(n, c64 ? 1 : 0);
@@ -373,11 +390,11 @@ int tune_shape(rsv_ctx* ctx, int n, bool c64, StepParams* sp, double* vmat, KSta
     b.out = z;
     TileMaps maps;
     if (!encode_tile_map(&maps.x, x, p.b, c64) || !encode_tile_map(&maps.z, z, p.b, c64)) continue;
-    bool ok = launch_tile(b, &maps, TileMode::kMatvecSecond, c64, false, p.grid_b, ctx->stream) == cudaSuccess;
-    cudaEventRecord(e0, ctx->stream);
+    bool ok = launch_tile(b, &maps, TileMode::kMatvecSecond, c64, false, p.grid_b, stream) == cudaSuccess;
+    cudaEventRecord(e0, stream);
     for (int r = 0; r < 3 && ok; ++r)
-      ok = launch_tile(b, &maps, TileMode::kMatvecSecond, c64, false, p.grid_b, ctx->stream) == cudaSuccess;
-    cudaEventRecord(e1, ctx->stream);
+      ok = launch_tile(b, &maps, TileMode::kMatvecSecond, c64, false, p.grid_b, stream) == cudaSuccess;
+    cudaEventRecord(e1, stream);
     if (!ok || cudaEventSynchronize(e1) != cudaSuccess) continue;
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
@@ -388,7 +405,7 @@ int tune_shape(rsv_ctx* ctx, int n, bool c64, StepParams* sp, double* vmat, KSta
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  cudaMemsetAsync(err_ptr(ks), 0, sizeof(int), ctx->stream);
+  cudaMemsetAsync(err_ptr(ks), 0, sizeof(int), stream);
   ctx->tuned_segment[key] = best;
   return best;
 }
@@ -407,6 +424,8 @@ rsv_status run_pass(rsv_ctx* ctx, TileArgs args, const TileMaps* maps, TileMode 
 // ---------------------------------------------------------------------------
 struct rsv_solver {
   rsv_ctx* ctx = nullptr;
+  cudaStream_t stream = nullptr;  // the context stream, or a served request's own stream
+  bool own_stream = false;        // destroy `stream` with the solver
   int n = 0;
   int precision = RSV_C128;
   bool c64 = false;
@@ -452,22 +471,22 @@ struct rsv_solver {
   rsv_status reset_to_initial() {
     const size_t vbytes = (size_t)dim * amp_bytes(precision);
     if (!init_host.empty()) {
-      RSV_CUDA(cudaMemcpyAsync(d_psi, init_host.data(), vbytes, cudaMemcpyHostToDevice, ctx->stream));
+      RSV_CUDA(cudaMemcpyAsync(d_psi, init_host.data(), vbytes, cudaMemcpyHostToDevice, stream));
     } else {
-      RSV_CUDA(cudaMemsetAsync(d_psi, 0, vbytes, ctx->stream));
+      RSV_CUDA(cudaMemsetAsync(d_psi, 0, vbytes, stream));
       const double one_d[2] = {1.0, 0.0};
       const float one_f[2] = {1.f, 0.f};
       RSV_CUDA(cudaMemcpyAsync(d_psi, c64 ? (const void*)one_f : (const void*)one_d, c64 ? sizeof(one_f) : sizeof(one_d),
-                               cudaMemcpyHostToDevice, ctx->stream));
+                               cudaMemcpyHostToDevice, stream));
     }
     std::vector<char> zero_ks(sizeof(KState), 0);
-    RSV_CUDA(cudaMemcpyAsync(d_ks, zero_ks.data(), sizeof(KState), cudaMemcpyHostToDevice, ctx->stream));
+    RSV_CUDA(cudaMemcpyAsync(d_ks, zero_ks.data(), sizeof(KState), cudaMemcpyHostToDevice, stream));
     done = 0;
     rows = 0;
     last_m = 0;
     RSV_TRY(observe_into_partials());
     RSV_TRY(record_row());
-    RSV_CUDA(cudaStreamSynchronize(ctx->stream));
+    RSV_CUDA(cudaStreamSynchronize(stream));
     return RSV_OK;
   }
 
@@ -477,7 +496,7 @@ struct rsv_solver {
     return RSV_OK;
   }
   ~rsv_solver() {
-    if (ctx) cudaStreamSynchronize(ctx->stream);
+    if (ctx) cudaStreamSynchronize(stream);
     for (auto& p : pending) {
       cudaEventDestroy(p.a);
       cudaEventDestroy(p.b);
@@ -485,6 +504,7 @@ struct rsv_solver {
     for (auto e : event_pool) cudaEventDestroy(e);
     for (void* p : owned) ctx->arena.release(p);
     if (h_ks) cudaFreeHost(h_ks);
+    if (own_stream && stream) cudaStreamDestroy(stream);
   }
 
   cudaEvent_t take_event() {
@@ -506,13 +526,13 @@ struct rsv_solver {
     if (profiling) {
       a = take_event();
       b = take_event();
-      RSV_CUDA(cudaEventRecord(a, ctx->stream));
+      RSV_CUDA(cudaEventRecord(a, stream));
     }
     cudaError_t e = fn();
     if (e != cudaSuccess) return fail(RSV_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
     stats.kernel_launches += 1;
     if (profiling) {
-      RSV_CUDA(cudaEventRecord(b, ctx->stream));
+      RSV_CUDA(cudaEventRecord(b, stream));
       pending.push_back({kind, bytes, a, b});
     }
     return RSV_OK;
@@ -534,8 +554,8 @@ struct rsv_solver {
   }
 
   rsv_status read_status() {
-    RSV_CUDA(cudaMemcpyAsync(h_ks, d_ks, kStatusBytes, cudaMemcpyDeviceToHost, ctx->stream));
-    RSV_CUDA(cudaStreamSynchronize(ctx->stream));
+    RSV_CUDA(cudaMemcpyAsync(h_ks, d_ks, kStatusBytes, cudaMemcpyDeviceToHost, stream));
+    RSV_CUDA(cudaStreamSynchronize(stream));
     if (profiling) drain_timings();
     return RSV_OK;
   }
@@ -552,7 +572,7 @@ struct rsv_solver {
     ca.partials = d_cpart;
     ca.combine = combine_flag;
     const double bytes = combine_flag ? vec_bytes() * (m + 1) : vec_bytes();
-    return launch(RSV_KERNEL_COMBINE, bytes, [&] { return launch_combine(ca, c64, plan.grid_c, ctx->stream); });
+    return launch(RSV_KERNEL_COMBINE, bytes, [&] { return launch_combine(ca, c64, plan.grid_c, stream); });
   }
 
   rsv_status observe_into_partials() { return combine(0, 0); }
@@ -566,7 +586,7 @@ struct rsv_solver {
     ba.new_tau = new_tau;
     ba.occ_out = occ_row;
     ba.reset_only = reset_only;
-    return launch(RSV_KERNEL_CONTROL, 0.0, [&] { return launch_begin(ba, ctx->stream); });
+    return launch(RSV_KERNEL_CONTROL, 0.0, [&] { return launch_begin(ba, stream); });
   }
 
   rsv_status record_row() {
@@ -602,17 +622,17 @@ struct rsv_solver {
     const double first_bytes = vec_bytes() * (j > 0 ? 4 : 3);
     if (!plan.two_pass) {
       RSV_TRY(launch(RSV_KERNEL_PASS_FIRST, first_bytes,
-                     [&] { return launch_tile(a, nullptr, TileMode::kLanczosSingle, c64, phi, plan.grid_a, ctx->stream); }));
+                     [&] { return launch_tile(a, nullptr, TileMode::kLanczosSingle, c64, phi, plan.grid_a, stream); }));
     } else {
       RSV_TRY(launch(RSV_KERNEL_PASS_FIRST, first_bytes,
-                     [&] { return launch_tile(a, nullptr, TileMode::kLanczosFirst, c64, phi, plan.grid_a, ctx->stream); }));
+                     [&] { return launch_tile(a, nullptr, TileMode::kLanczosFirst, c64, phi, plan.grid_a, stream); }));
       TileArgs b = base_args(plan.b, step);
       b.xin = basis[j];
       b.out = u_out;
       RSV_TRY(launch(RSV_KERNEL_PASS_SECOND, vec_bytes() * 3,
                      [&] {
                        TileMaps maps{map_basis[j], map_u[j & 1]};
-                       return launch_tile(b, &maps, TileMode::kLanczosSecond, c64, phi, plan.grid_b, ctx->stream);
+                       return launch_tile(b, &maps, TileMode::kLanczosSecond, c64, phi, plan.grid_b, stream);
                      }));
     }
     return RSV_OK;
@@ -623,7 +643,7 @@ struct rsv_solver {
     const double tau = h_sp[k].tau;
     RSV_TRY(begin(tau, 0, nullptr));
     RSV_TRY(launch(RSV_KERNEL_CONTROL, 0.0, [&] {
-      return launch_diag_table(d_sp + k, d_vmat, n, plan.a.L, plan.a.num_tiles, d_diag, ctx->stream);
+      return launch_diag_table(d_sp + k, d_vmat, n, plan.a.L, plan.a.num_tiles, d_diag, stream);
     }));
     const int m_max = cfg.m_max;
     int restarts = 0;
@@ -641,7 +661,7 @@ struct rsv_solver {
       bool finished = false;
       for (; j < m_max; ++j) {
         RSV_TRY(iteration(j, k));
-        RSV_TRY(launch(RSV_KERNEL_CONTROL, 0.0, [&] { return launch_scalar(sa, ctx->stream); }));
+        RSV_TRY(launch(RSV_KERNEL_CONTROL, 0.0, [&] { return launch_scalar(sa, stream); }));
         if (j + 1 >= check_from) {
           RSV_TRY(read_status());
           if (h_ks->error) return fail(RSV_ERR_TIMEOUT, "a device-side wait timed out (kernel aborted)");
@@ -678,6 +698,36 @@ struct rsv_result {
   rsv_solver* solver = nullptr;
   std::vector<double> occ;
   int rows = 0;
+  double wait_s = 0.0;     // served requests: submission to admission
+  double service_s = 0.0;  // admission (or call) to completion
+};
+
+// A prepared H (Eq. (3)) for repeated y = H x: tables and per-tile diagonal
+// rows are built once, each apply enqueues only the streaming passes.
+struct rsv_hamiltonian {
+  rsv_ctx* ctx = nullptr;
+  int n = 0;
+  bool c64 = true, phi = false;
+  Plan plan;
+  StepParams* d_sp = nullptr;
+  double* d_vmat = nullptr;
+  void* d_qtab = nullptr;
+  double* d_diag = nullptr;
+  KState* d_ks = nullptr;  // error word of the bounded waits
+  double* d_part = nullptr;
+  const void* map_x = nullptr;  // operands the cached tensor maps describe
+  const void* map_y = nullptr;
+  TileMaps maps;
+  std::vector<void*> owned;
+  rsv_status alloc(size_t bytes, void** p) {
+    RSV_TRY(ctx->arena.alloc(bytes, p));
+    owned.push_back(*p);
+    return RSV_OK;
+  }
+  ~rsv_hamiltonian() {
+    if (ctx && ctx->stream) cudaStreamSynchronize(ctx->stream);
+    for (void* p : owned) ctx->arena.release(p);
+  }
 };
 
 // ---------------------------------------------------------------------------
@@ -734,8 +784,11 @@ void rsv_destroy(rsv_ctx* ctx) {
   cudaSetDevice(ctx->device);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   // free what the caller left open (their handles become invalid)
+  while (!ctx->servers.empty()) rsv_server_destroy(*ctx->servers.begin());
+  while (!ctx->hamiltonians.empty()) rsv_hamiltonian_destroy(*ctx->hamiltonians.begin());
   while (!ctx->results.empty()) rsv_result_free(*ctx->results.begin());
   while (!ctx->solvers.empty()) rsv_solver_destroy(*ctx->solvers.begin());
+  while (!ctx->batches.empty()) rsv_batch_destroy(*ctx->batches.begin());
   ctx->arena.release(ctx->d_sp);
   ctx->arena.release(ctx->d_vmat);
   ctx->arena.release(ctx->d_qtab);
@@ -752,8 +805,11 @@ size_t rsv_footprint_bytes(int32_t n_atoms, int32_t precision, int32_t m_max) {
   if (m_max <= 0) m_max = 30;
   const size_t D = size_t(1) << n_atoms;
   const size_t vec = D * (size_t)amp_bytes(precision);
-  // state + m_max basis vectors + two work vectors + tables/partials
-  return vec * (size_t)(m_max + 3) + (size_t(1) << 20);
+  const int L = precision == RSV_C64 ? kTileBitsC64 : kTileBitsC128;
+  const size_t diag = sizeof(double) * kDiagStride * (n_atoms > L ? size_t(1) << (n_atoms - L) : 1);
+  // state + m_max basis vectors + two work vectors + per-tile diagonal rows +
+  // parameter tables, partial sums and allocation rounding
+  return vec * (size_t)(m_max + 3) + diag + (size_t(2) << 20);
 }
 
 rsv_status rsv_pair_energies(int32_t n_atoms, int32_t dim, const double* positions_um, double c6, double* v_out) {
@@ -877,6 +933,121 @@ rsv_status rsv_apply_hamiltonian(rsv_ctx* ctx, int32_t n_atoms, int32_t precisio
   return RSV_OK;
 }
 
+rsv_status rsv_hamiltonian_create(rsv_ctx* ctx, int32_t n_atoms, int32_t precision, const double* v_pairs,
+                                  const double* omega, const double* delta, const double* phi, rsv_hamiltonian** out) {
+  g_last_error.clear();
+  if (!ctx || !v_pairs || !omega || !delta || !out) return fail(RSV_ERR_INVALID_ARG, "NULL argument");
+  *out = nullptr;
+  if (n_atoms < 1 || n_atoms > 31) return fail(RSV_ERR_INVALID_ARG, "n_atoms out of range");
+  if (precision != RSV_C64 && precision != RSV_C128) return fail(RSV_ERR_INVALID_ARG, "bad precision");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  cudaSetDevice(ctx->device);
+  std::unique_ptr<rsv_hamiltonian> h(new rsv_hamiltonian());
+  h->ctx = ctx;
+  h->n = n_atoms;
+  h->c64 = precision == RSV_C64;
+  StepParams sp{};
+  std::memset(&sp, 0, sizeof(sp));
+  for (int i = 0; i < n_atoms; ++i) {
+    const int q = n_atoms - 1 - i;
+    sp.half_omega[q] = 0.5 * omega[i];
+    sp.delta[q] = delta[i];
+    sp.phi[q] = phi ? phi[i] : 0.0;
+    h->phi = h->phi || (phi && phi[i] != 0.0);
+  }
+  sp.has_phi = h->phi;
+  const std::vector<double> vb = to_bit_matrix(n_atoms, v_pairs);
+  const int shape = shape_for(ctx, n_atoms, h->c64);
+  h->plan = make_plan(n_atoms, h->c64, ctx->num_sms, shape / 16, shape % 16);
+  if (h->plan.two_pass && h->plan.b.nG > kMaxGBits) return fail(RSV_ERR_INVALID_ARG, "n_atoms too large");
+  RSV_TRY(h->alloc(sizeof(StepParams), (void**)&h->d_sp));
+  RSV_TRY(h->alloc(sizeof(double) * kMaxAtoms * kMaxAtoms, (void**)&h->d_vmat));
+  RSV_TRY(h->alloc((h->c64 ? sizeof(float) : sizeof(double)) << h->plan.L_a, &h->d_qtab));
+  RSV_TRY(h->alloc(sizeof(double) * kDiagStride * h->plan.a.num_tiles, (void**)&h->d_diag));
+  RSV_TRY(h->alloc(sizeof(KState), (void**)&h->d_ks));
+  RSV_TRY(h->alloc(sizeof(double) * partials_doubles(ctx->num_sms), (void**)&h->d_part));
+  RSV_CUDA(cudaMemcpyAsync(h->d_sp, &sp, sizeof(sp), cudaMemcpyHostToDevice, ctx->stream));
+  RSV_CUDA(cudaMemcpyAsync(h->d_vmat, vb.data(), vb.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  if (h->c64) {
+    const std::vector<float> q = q_table<float>(vb, h->plan.L_a);
+    RSV_CUDA(cudaMemcpyAsync(h->d_qtab, q.data(), q.size() * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+    RSV_CUDA(cudaStreamSynchronize(ctx->stream));
+  } else {
+    const std::vector<double> q = q_table<double>(vb, h->plan.L_a);
+    RSV_CUDA(cudaMemcpyAsync(h->d_qtab, q.data(), q.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    RSV_CUDA(cudaStreamSynchronize(ctx->stream));
+  }
+  RSV_CUDA(cudaMemsetAsync(h->d_ks, 0, sizeof(KState), ctx->stream));
+  RSV_CUDA(launch_diag_table(h->d_sp, h->d_vmat, n_atoms, h->plan.a.L, h->plan.a.num_tiles, h->d_diag, ctx->stream));
+  RSV_CUDA(cudaStreamSynchronize(ctx->stream));
+  ctx->hamiltonians.insert(h.get());
+  *out = h.release();
+  return RSV_OK;
+}
+
+rsv_status rsv_hamiltonian_apply(rsv_hamiltonian* h, const void* x_dev, void* y_dev) {
+  g_last_error.clear();
+  if (!h || !x_dev || !y_dev) return fail(RSV_ERR_INVALID_ARG, "NULL argument");
+  if ((reinterpret_cast<uintptr_t>(x_dev) | reinterpret_cast<uintptr_t>(y_dev)) & 15)
+    return fail(RSV_ERR_INVALID_ARG, "device buffers must be 16-byte aligned");
+  if (x_dev == y_dev) return fail(RSV_ERR_INVALID_ARG, "x and y must not alias");
+  rsv_ctx* ctx = h->ctx;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  cudaSetDevice(ctx->device);
+  TileArgs a = h->plan.a;
+  a.sp = h->d_sp;
+  a.vmat = h->d_vmat;
+  a.qtab = h->d_qtab;
+  a.ks = h->d_ks;
+  a.partials = h->d_part;
+  a.err = err_ptr(h->d_ks);
+  a.diag = h->d_diag;
+  a.xin = x_dev;
+  a.out = y_dev;
+  RSV_TRY(run_pass(ctx, a, nullptr, TileMode::kMatvecFirst, h->c64, h->phi, h->plan.grid_a));
+  if (h->plan.two_pass) {
+    if (x_dev != h->map_x || y_dev != h->map_y) {
+      if (!encode_tile_map(&h->maps.x, x_dev, h->plan.b, h->c64) ||
+          !encode_tile_map(&h->maps.z, y_dev, h->plan.b, h->c64))
+        return fail(RSV_ERR_CUDA, "tensor map encoding failed");
+      h->map_x = x_dev;
+      h->map_y = y_dev;
+    }
+    TileArgs b = h->plan.b;
+    b.sp = h->d_sp;
+    b.vmat = h->d_vmat;
+    b.ks = h->d_ks;
+    b.partials = h->d_part;
+    b.err = err_ptr(h->d_ks);
+    b.xin = x_dev;
+    b.out = y_dev;
+    RSV_TRY(run_pass(ctx, b, &h->maps, TileMode::kMatvecSecond, h->c64, h->phi, h->plan.grid_b));
+  }
+  return RSV_OK;
+}
+
+rsv_status rsv_hamiltonian_sync(rsv_hamiltonian* h) {
+  g_last_error.clear();
+  if (!h) return fail(RSV_ERR_INVALID_ARG, "NULL operator");
+  rsv_ctx* ctx = h->ctx;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  cudaSetDevice(ctx->device);
+  int err = 0;
+  RSV_CUDA(cudaMemcpyAsync(&err, err_ptr(h->d_ks), sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  RSV_CUDA(cudaStreamSynchronize(ctx->stream));
+  if (err) return fail(RSV_ERR_TIMEOUT, "a device-side wait timed out (kernel aborted)");
+  return RSV_OK;
+}
+
+void rsv_hamiltonian_destroy(rsv_hamiltonian* h) {
+  if (!h) return;
+  {
+    std::lock_guard<std::mutex> lk(h->ctx->mu);
+    h->ctx->hamiltonians.erase(h);
+  }
+  delete h;
+}
+
 rsv_status rsv_observe(rsv_ctx* ctx, int32_t n_atoms, int32_t precision, const void* psi_dev, double* norm2_out,
                        double* occ_out) {
   g_last_error.clear();
@@ -967,7 +1138,8 @@ rsv_status rsv_sample(rsv_ctx* ctx, int32_t n_atoms, int32_t precision, const vo
   return RSV_OK;
 }
 
-rsv_status rsv_solver_create(rsv_ctx* ctx, const rsv_problem* problem, const rsv_config* config, rsv_solver** out) {
+static rsv_status solver_create(rsv_ctx* ctx, const rsv_problem* problem, const rsv_config* config,
+                                cudaStream_t stream, rsv_solver** out) {
   g_last_error.clear();
   if (!ctx || !config || !out) return fail(RSV_ERR_INVALID_ARG, "NULL argument");
   *out = nullptr;
@@ -985,12 +1157,13 @@ rsv_status rsv_solver_create(rsv_ctx* ctx, const rsv_problem* problem, const rsv
   std::lock_guard<std::mutex> lk(ctx->mu);
   cudaSetDevice(ctx->device);
   if (ctx->arena.cap() > 0 &&
-      rsv_footprint_bytes(n, cfg.precision, cfg.m_max) > ctx->arena.cap() - ctx->arena.used())
+      solver_bytes(problem, cfg) > ctx->arena.cap() - ctx->arena.used())
     return fail(RSV_ERR_OUT_OF_MEMORY, "footprint exceeds the free arena");
   std::vector<double> v_atoms;
   RSV_TRY(pair_energies(n, problem->dim, problem->positions_um, problem->c6, v_atoms));
   auto s = new rsv_solver();
   s->ctx = ctx;
+  s->stream = stream ? stream : ctx->stream;
   s->n = n;
   s->precision = cfg.precision;
   s->c64 = cfg.precision == RSV_C64;
@@ -1031,7 +1204,7 @@ rsv_status rsv_solver_create(rsv_ctx* ctx, const rsv_problem* problem, const rsv
     return fail(RSV_ERR_CUDA, std::string("cudaMallocHost: ") + cudaGetErrorString(e));
   }
   if (s->plan.two_pass) {
-    const int shape = tune_shape(ctx, n, s->c64, s->d_sp, s->d_vmat, s->d_ks, s->d_part, s->basis[0], s->d_u[0]);
+    const int shape = tune_shape(ctx, s->stream, n, s->c64, s->d_sp, s->d_vmat, s->d_ks, s->d_part, s->basis[0], s->d_u[0]);
     s->plan = make_plan(n, s->c64, ctx->num_sms, shape / 16, shape % 16);
     s->map_basis.resize(cfg.m_max);
     bool ok = true;
@@ -1048,26 +1221,26 @@ rsv_status rsv_solver_create(rsv_ctx* ctx, const rsv_problem* problem, const rsv
     return r;
   };
   std::vector<char> zero_ks(sizeof(KState), 0);
-  if (cudaMemcpyAsync(s->d_sp, s->h_sp.data(), sizeof(StepParams) * s->nsteps, cudaMemcpyHostToDevice, ctx->stream) !=
+  if (cudaMemcpyAsync(s->d_sp, s->h_sp.data(), sizeof(StepParams) * s->nsteps, cudaMemcpyHostToDevice, s->stream) !=
           cudaSuccess ||
-      cudaMemcpyAsync(s->d_vmat, vb.data(), vb.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream) !=
+      cudaMemcpyAsync(s->d_vmat, vb.data(), vb.size() * sizeof(double), cudaMemcpyHostToDevice, s->stream) !=
           cudaSuccess ||
-      cudaMemcpyAsync(s->d_basis, s->basis.data(), sizeof(void*) * cfg.m_max, cudaMemcpyHostToDevice, ctx->stream) !=
+      cudaMemcpyAsync(s->d_basis, s->basis.data(), sizeof(void*) * cfg.m_max, cudaMemcpyHostToDevice, s->stream) !=
           cudaSuccess ||
-      cudaMemcpyAsync(s->d_ks, zero_ks.data(), sizeof(KState), cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess)
+      cudaMemcpyAsync(s->d_ks, zero_ks.data(), sizeof(KState), cudaMemcpyHostToDevice, s->stream) != cudaSuccess)
     return fin(fail(RSV_ERR_CUDA, "upload failed"));
   if (s->c64) {
     auto q = q_table<float>(vb, s->plan.L_a);
-    if (cudaMemcpyAsync(s->d_qtab, q.data(), q.size() * sizeof(float), cudaMemcpyHostToDevice, ctx->stream) !=
+    if (cudaMemcpyAsync(s->d_qtab, q.data(), q.size() * sizeof(float), cudaMemcpyHostToDevice, s->stream) !=
         cudaSuccess)
       return fin(fail(RSV_ERR_CUDA, "upload failed"));
-    cudaStreamSynchronize(ctx->stream);
+    cudaStreamSynchronize(s->stream);
   } else {
     auto q = q_table<double>(vb, s->plan.L_a);
-    if (cudaMemcpyAsync(s->d_qtab, q.data(), q.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream) !=
+    if (cudaMemcpyAsync(s->d_qtab, q.data(), q.size() * sizeof(double), cudaMemcpyHostToDevice, s->stream) !=
         cudaSuccess)
       return fin(fail(RSV_ERR_CUDA, "upload failed"));
-    cudaStreamSynchronize(ctx->stream);
+    cudaStreamSynchronize(s->stream);
   }
   if (problem->initial_state) {
     const char* p = static_cast<const char*>(problem->initial_state);
@@ -1078,6 +1251,10 @@ rsv_status rsv_solver_create(rsv_ctx* ctx, const rsv_problem* problem, const rsv
   ctx->solvers.insert(s);
   *out = s;
   return RSV_OK;
+}
+
+rsv_status rsv_solver_create(rsv_ctx* ctx, const rsv_problem* problem, const rsv_config* config, rsv_solver** out) {
+  return solver_create(ctx, problem, config, nullptr, out);
 }
 
 rsv_status rsv_solver_rewind(rsv_solver* s) {
@@ -1097,17 +1274,23 @@ void rsv_solver_destroy(rsv_solver* s) {
   delete s;
 }
 
+// Advances a solver on its own stream. Callers serialise access to `s`; the
+// context lock is not needed (the arena has its own).
+static rsv_status solver_step(rsv_solver* s, int32_t n_steps) {
+  cudaSetDevice(s->ctx->device);
+  const auto t0 = std::chrono::steady_clock::now();
+  for (int i = 0; i < n_steps && s->done < s->nsteps; ++i) RSV_TRY(s->step_once());
+  RSV_CUDA(cudaStreamSynchronize(s->stream));
+  if (s->profiling) s->drain_timings();
+  s->stats.seconds += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  return RSV_OK;
+}
+
 rsv_status rsv_solver_step(rsv_solver* s, int32_t n_steps) {
   g_last_error.clear();
   if (!s || n_steps < 0) return fail(RSV_ERR_INVALID_ARG, "bad arguments");
   std::lock_guard<std::mutex> lk(s->ctx->mu);
-  cudaSetDevice(s->ctx->device);
-  const auto t0 = std::chrono::steady_clock::now();
-  for (int i = 0; i < n_steps && s->done < s->nsteps; ++i) RSV_TRY(s->step_once());
-  RSV_CUDA(cudaStreamSynchronize(s->ctx->stream));
-  if (s->profiling) s->drain_timings();
-  s->stats.seconds += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-  return RSV_OK;
+  return solver_step(s, n_steps);
 }
 
 rsv_status rsv_solver_progress(const rsv_solver* s, int32_t* done, int32_t* total) {
@@ -1129,8 +1312,8 @@ rsv_status rsv_solver_get_state(rsv_solver* s, void* host_dst, size_t bytes) {
   if (!s || !host_dst) return fail(RSV_ERR_INVALID_ARG, "NULL argument");
   if (bytes != (size_t)s->dim * amp_bytes(s->precision)) return fail(RSV_ERR_INVALID_ARG, "size mismatch");
   std::lock_guard<std::mutex> lk(s->ctx->mu);
-  RSV_CUDA(cudaMemcpyAsync(host_dst, s->d_psi, bytes, cudaMemcpyDeviceToHost, s->ctx->stream));
-  RSV_CUDA(cudaStreamSynchronize(s->ctx->stream));
+  RSV_CUDA(cudaMemcpyAsync(host_dst, s->d_psi, bytes, cudaMemcpyDeviceToHost, s->stream));
+  RSV_CUDA(cudaStreamSynchronize(s->stream));
   return RSV_OK;
 }
 
@@ -1139,9 +1322,9 @@ rsv_status rsv_solver_set_state(rsv_solver* s, const void* host_src, size_t byte
   if (!s || !host_src) return fail(RSV_ERR_INVALID_ARG, "NULL argument");
   if (bytes != (size_t)s->dim * amp_bytes(s->precision)) return fail(RSV_ERR_INVALID_ARG, "size mismatch");
   std::lock_guard<std::mutex> lk(s->ctx->mu);
-  RSV_CUDA(cudaMemcpyAsync(s->d_psi, host_src, bytes, cudaMemcpyHostToDevice, s->ctx->stream));
+  RSV_CUDA(cudaMemcpyAsync(s->d_psi, host_src, bytes, cudaMemcpyHostToDevice, s->stream));
   RSV_TRY(s->observe_into_partials());
-  RSV_CUDA(cudaStreamSynchronize(s->ctx->stream));
+  RSV_CUDA(cudaStreamSynchronize(s->stream));
   return RSV_OK;
 }
 
@@ -1150,9 +1333,9 @@ rsv_status rsv_solver_set_state_device(rsv_solver* s, const void* dev_src, size_
   if (!s || !dev_src) return fail(RSV_ERR_INVALID_ARG, "NULL argument");
   if (bytes != (size_t)s->dim * amp_bytes(s->precision)) return fail(RSV_ERR_INVALID_ARG, "size mismatch");
   std::lock_guard<std::mutex> lk(s->ctx->mu);
-  RSV_CUDA(cudaMemcpyAsync(s->d_psi, dev_src, bytes, cudaMemcpyDeviceToDevice, s->ctx->stream));
+  RSV_CUDA(cudaMemcpyAsync(s->d_psi, dev_src, bytes, cudaMemcpyDeviceToDevice, s->stream));
   RSV_TRY(s->observe_into_partials());
-  RSV_CUDA(cudaStreamSynchronize(s->ctx->stream));
+  RSV_CUDA(cudaStreamSynchronize(s->stream));
   return RSV_OK;
 }
 
@@ -1163,8 +1346,8 @@ rsv_status rsv_solver_occupations(rsv_solver* s, double* dst, int32_t capacity_r
   if (!dst) return RSV_OK;
   const int rows = std::min(capacity_rows, s->rows);
   std::lock_guard<std::mutex> lk(s->ctx->mu);
-  RSV_CUDA(cudaMemcpyAsync(dst, s->d_occ, sizeof(double) * s->n * rows, cudaMemcpyDeviceToHost, s->ctx->stream));
-  RSV_CUDA(cudaStreamSynchronize(s->ctx->stream));
+  RSV_CUDA(cudaMemcpyAsync(dst, s->d_occ, sizeof(double) * s->n * rows, cudaMemcpyDeviceToHost, s->stream));
+  RSV_CUDA(cudaStreamSynchronize(s->stream));
   return RSV_OK;
 }
 
@@ -1172,7 +1355,7 @@ rsv_status rsv_solver_set_profiling(rsv_solver* s, int32_t on) {
   g_last_error.clear();
   if (!s) return fail(RSV_ERR_INVALID_ARG, "NULL solver");
   std::lock_guard<std::mutex> lk(s->ctx->mu);
-  RSV_CUDA(cudaStreamSynchronize(s->ctx->stream));
+  RSV_CUDA(cudaStreamSynchronize(s->stream));
   s->drain_timings();
   s->profiling = on != 0;
   if (s->profiling) s->ktimes = rsv_kernel_times{};
@@ -1192,6 +1375,30 @@ rsv_status rsv_solver_stats(const rsv_solver* s, rsv_stats* out) {
   out->segment_bits = s->plan.two_pass ? s->plan.b.c : s->plan.a.c;
   out->l2_partner_bits = s->plan.two_pass ? s->plan.b.nG : s->plan.a.nG;
   out->tile_order_bits = s->plan.two_pass ? s->plan.b.f1_fast : 0;
+  out->krylov_dim_max = s->cfg.m_max;
+  return RSV_OK;
+}
+
+// A finished solver becomes a result (owned by the context until freed).
+static rsv_status make_result(rsv_solver* s, rsv_result** out) {
+  rsv_ctx* ctx = s->ctx;
+  auto r = new rsv_result();
+  r->solver = s;
+  r->service_s = s->stats.seconds;
+  {
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->solvers.erase(s);
+    ctx->results.insert(r);
+  }
+  r->rows = s->rows;
+  r->occ.resize((size_t)s->rows * s->n);
+  int32_t rows = 0;
+  const rsv_status st = rsv_solver_occupations(s, r->occ.data(), s->rows, &rows);
+  if (st != RSV_OK) {
+    rsv_result_free(r);
+    return st;
+  }
+  *out = r;
   return RSV_OK;
 }
 
@@ -1206,23 +1413,7 @@ rsv_status rsv_run(rsv_ctx* ctx, const rsv_problem* problem, const rsv_config* c
     rsv_solver_destroy(s);
     return st;
   }
-  auto r = new rsv_result();
-  r->solver = s;
-  {
-    std::lock_guard<std::mutex> lk(ctx->mu);
-    ctx->solvers.erase(s);
-    ctx->results.insert(r);
-  }
-  r->rows = s->rows;
-  r->occ.resize((size_t)s->rows * s->n);
-  int32_t rows = 0;
-  st = rsv_solver_occupations(s, r->occ.data(), s->rows, &rows);
-  if (st != RSV_OK) {
-    rsv_result_free(r);
-    return st;
-  }
-  *out = r;
-  return RSV_OK;
+  return make_result(s, out);
 }
 
 rsv_status rsv_result_state(const rsv_result* r, void* host_dst, size_t bytes) {
@@ -1255,6 +1446,13 @@ rsv_status rsv_result_stats(const rsv_result* r, rsv_stats* out) {
   return rsv_solver_stats(r->solver, out);
 }
 
+rsv_status rsv_result_times(const rsv_result* r, double* wait_s, double* service_s) {
+  if (!r) return fail(RSV_ERR_INVALID_ARG, "NULL result");
+  if (wait_s) *wait_s = r->wait_s;
+  if (service_s) *service_s = r->service_s;
+  return RSV_OK;
+}
+
 void rsv_result_free(rsv_result* r) {
   if (!r) return;
   {
@@ -1263,6 +1461,620 @@ void rsv_result_free(rsv_result* r) {
   }
   delete r->solver;  // owned by the result, not in the context's solver set
   delete r;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batch: many independent registers evolved by one persistent launch
+// (batch_kernels.cu), replayed from a captured CUDA graph.
+// ---------------------------------------------------------------------------
+struct rsv_batch {
+  rsv_ctx* ctx = nullptr;
+  int count = 0;
+  rsv_config cfg{};
+  bool c64 = true;
+  int nmax = 0;
+  int grid = 0;
+  int blocks_per_sm = 0;
+  int64_t work_stride = 0;
+  size_t state_amps = 0;
+  std::vector<BatchItem> items;
+  std::vector<int> order;
+  std::vector<BatchOut> out;
+  bool have_out = false;
+  int runs = 0;
+  float last_ms = 0.f;
+  float tuned_ms = 0.f;  // sample time of the chosen Krylov depth (autotuned batches)
+  std::vector<void*> allocs;
+  BatchItem* d_items = nullptr;
+  int* d_order = nullptr;
+  int* d_next = nullptr;
+  void* d_states = nullptr;
+  void* d_init = nullptr;
+  double* d_params = nullptr;
+  double* d_vmat = nullptr;
+  double* d_occ = nullptr;
+  BatchOut* d_out = nullptr;
+  void* d_work = nullptr;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t ev_in = nullptr, ev0 = nullptr, ev1 = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+
+  rsv_status alloc(size_t bytes, void** p) {
+    RSV_TRY(ctx->arena.alloc(bytes, p));
+    allocs.push_back(*p);
+    return RSV_OK;
+  }
+  ~rsv_batch() {
+    if (stream) cudaStreamSynchronize(stream);
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    for (void* p : allocs) ctx->arena.release(p);
+    if (ev_in) cudaEventDestroy(ev_in);
+    if (ev0) cudaEventDestroy(ev0);
+    if (ev1) cudaEventDestroy(ev1);
+    if (stream) cudaStreamDestroy(stream);
+  }
+  BatchArgs args() const {
+    BatchArgs a{};
+    a.items = d_items;
+    a.order = d_order;
+    a.count = count;
+    a.next = d_next;
+    a.states = d_states;
+    a.params = d_params;
+    a.vmat = d_vmat;
+    a.occ = d_occ;
+    a.out = d_out;
+    a.work = d_work;
+    a.work_stride = work_stride;
+    a.m_max = cfg.m_max;
+    a.max_substeps = cfg.max_substeps;
+    a.tol = cfg.krylov_tol;
+    a.breakdown = 1e-13;
+    return a;
+  }
+};
+
+namespace {
+
+constexpr int kBatchTuneMax = 40;
+
+// Krylov-depth autotuner of a batch: evolves a sample of the registers (spread
+// over the largest-first order) with each candidate m_max and keeps the
+// fastest. A larger m_max means fewer substeps but more FP64 exponentials per
+// step and a larger workspace; the best value depends on the registers'
+// spectra and time steps. The workspace is then shrunk to the chosen depth.
+rsv_status batch_tune_krylov(rsv_batch* b) {
+  static const int cand[] = {12, 16, 20, 24, 32, kBatchTuneMax};
+  const int ns = std::min(b->count, 48);
+  std::vector<int> sample(ns);
+  for (int i = 0; i < ns; ++i) sample[i] = b->order[(size_t)i * b->count / ns];
+  int* d_sample = nullptr;
+  RSV_TRY(b->alloc(sizeof(int) * ns, (void**)&d_sample));
+  RSV_CUDA(cudaMemcpyAsync(d_sample, sample.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, b->stream));
+  const size_t sbytes = b->state_amps * amp_bytes(b->cfg.precision);
+  int best = b->cfg.m_max;
+  float best_ms = 1e30f;
+  for (int c = -1; c < (int)(sizeof(cand) / sizeof(cand[0])); ++c) {
+    BatchArgs a = b->args();
+    a.order = d_sample;
+    a.count = ns;
+    a.m_max = cand[c < 0 ? 0 : c];  // c = -1: warm-up launch
+    RSV_CUDA(cudaMemcpyAsync(b->d_states, b->d_init, sbytes, cudaMemcpyDeviceToDevice, b->stream));
+    RSV_CUDA(cudaMemsetAsync(b->d_next, 0, sizeof(int), b->stream));
+    RSV_CUDA(cudaEventRecord(b->ev0, b->stream));
+    RSV_CUDA(launch_batch(a, b->c64, std::min(ns, b->grid), b->stream));
+    RSV_CUDA(cudaEventRecord(b->ev1, b->stream));
+    RSV_CUDA(cudaStreamSynchronize(b->stream));
+    float ms = 0.f;
+    RSV_CUDA(cudaEventElapsedTime(&ms, b->ev0, b->ev1));
+    std::vector<BatchOut> o(b->count);
+    RSV_CUDA(cudaMemcpy(o.data(), b->d_out, sizeof(BatchOut) * b->count, cudaMemcpyDeviceToHost));
+    bool ok = true;
+    for (int i : sample) ok = ok && o[i].status == 0;
+    if (c >= 0 && ok && ms < best_ms) {
+      best_ms = ms;
+      best = a.m_max;
+    }
+  }
+  b->cfg.m_max = best;
+  b->tuned_ms = best_ms;
+  // shrink the workspace to the chosen depth
+  const int64_t stride = (int64_t)(best + 1) << b->nmax;
+  if (stride < b->work_stride) {
+    const size_t bytes = (size_t)stride * b->grid * amp_bytes(b->cfg.precision);
+    void* w = nullptr;
+    if (b->ctx->arena.alloc(bytes, &w) == RSV_OK) {
+      b->ctx->arena.release(b->d_work);
+      b->allocs.erase(std::find(b->allocs.begin(), b->allocs.end(), b->d_work));
+      b->allocs.push_back(w);
+      b->d_work = w;
+      b->work_stride = stride;
+    }
+  }
+  return RSV_OK;
+}
+
+rsv_status batch_capture(rsv_batch* b) {
+  const size_t sbytes = b->state_amps * amp_bytes(b->cfg.precision);
+  RSV_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = cudaMemcpyAsync(b->d_states, b->d_init, sbytes, cudaMemcpyDeviceToDevice, b->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->d_next, 0, sizeof(int), b->stream);
+  if (e == cudaSuccess) e = launch_batch(b->args(), b->c64, b->grid, b->stream);
+  cudaGraph_t g = nullptr;
+  const cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
+  if (e != cudaSuccess || e2 != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return fail(RSV_ERR_CUDA, std::string("batch graph capture: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
+  }
+  b->graph = g;
+  RSV_CUDA(cudaGraphInstantiate(&b->exec, g, 0));
+  return RSV_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+rsv_status rsv_batch_create(rsv_ctx* ctx, const rsv_problem* problems, int32_t count, const rsv_config* config,
+                            rsv_batch** out) {
+  g_last_error.clear();
+  if (!ctx || !problems || !config || !out) return fail(RSV_ERR_INVALID_ARG, "NULL argument");
+  *out = nullptr;
+  if (count < 1) return fail(RSV_ERR_INVALID_ARG, "count must be >= 1");
+  rsv_config cfg = *config;
+  if (cfg.dt_ns < 1) return fail(RSV_ERR_INVALID_ARG, "dt_ns must be >= 1");
+  if (cfg.precision != RSV_C64 && cfg.precision != RSV_C128) return fail(RSV_ERR_INVALID_ARG, "bad precision");
+  const bool tune_m = cfg.m_max < 0;
+  if (cfg.m_max == 0) cfg.m_max = 30;
+  if (tune_m) cfg.m_max = kBatchTuneMax;
+  if (cfg.m_max < 2 || cfg.m_max > kMaxKrylov) return fail(RSV_ERR_INVALID_ARG, "m_max must be in [2, 64]");
+  if (cfg.krylov_tol <= 0.0) cfg.krylov_tol = cfg.precision == RSV_C64 ? 1e-7 : 1e-12;
+  if (cfg.max_substeps <= 0) cfg.max_substeps = 64;
+  if (cfg.obs_stride < 0) return fail(RSV_ERR_INVALID_ARG, "obs_stride must be >= 0");
+  const int64_t ab = amp_bytes(cfg.precision);
+  std::unique_ptr<rsv_batch> b(new rsv_batch());
+  b->ctx = ctx;
+  b->count = count;
+  b->cfg = cfg;
+  b->c64 = cfg.precision == RSV_C64;
+  // host tables
+  std::vector<double> params, vmat;
+  std::vector<char> init;
+  size_t occ_doubles = 0;
+  b->items.resize(count);
+  for (int r = 0; r < count; ++r) {
+    const rsv_problem* p = problems + r;
+    RSV_TRY(validate_problem(p));
+    const int n = p->n_atoms;
+    if (n > kBatchMaxAtoms)
+      return fail(RSV_ERR_INVALID_ARG, "problem " + std::to_string(r) + ": n_atoms = " + std::to_string(n) +
+                                           " exceeds the batched limit of " + std::to_string(kBatchMaxAtoms));
+    std::vector<double> v_atoms;
+    RSV_TRY(pair_energies(n, p->dim, p->positions_um, p->c6, v_atoms));
+    std::vector<StepParams> sp;
+    RSV_TRY(step_params(p, cfg.dt_ns, sp));
+    BatchItem& it = b->items[r];
+    std::memset(&it, 0, sizeof(it));
+    it.n = n;
+    it.steps = (int)sp.size();
+    it.obs_stride = cfg.obs_stride;
+    it.has_phi = any_phi(sp, n) ? 1 : 0;
+    it.occ_rows = (cfg.obs_stride > 0 ? it.steps / cfg.obs_stride : 0) + 2;
+    it.state_off = (int64_t)b->state_amps;
+    it.param_off = (int64_t)params.size();
+    it.vmat_off = (int64_t)vmat.size();
+    it.occ_off = (int64_t)occ_doubles;
+    for (const StepParams& s : sp) {
+      params.push_back(s.tau);
+      for (int q = 0; q < n; ++q) params.push_back(2.0 * s.half_omega[q]);
+      for (int q = 0; q < n; ++q) params.push_back(s.delta[q]);
+      for (int q = 0; q < n; ++q) params.push_back(s.phi[q]);
+    }
+    for (int q = 0; q < n; ++q)
+      for (int r2 = 0; r2 < n; ++r2) vmat.push_back(v_atoms[(size_t)(n - 1 - q) * n + (n - 1 - r2)]);
+    occ_doubles += (size_t)it.occ_rows * n;
+    const size_t D = size_t(1) << n;
+    const size_t old = init.size();
+    init.resize(old + D * ab, 0);
+    if (p->initial_state) {
+      std::memcpy(init.data() + old, p->initial_state, D * ab);
+    } else if (b->c64) {
+      const float one = 1.0f;
+      std::memcpy(init.data() + old, &one, sizeof(float));
+    } else {
+      const double one = 1.0;
+      std::memcpy(init.data() + old, &one, sizeof(double));
+    }
+    b->state_amps += D;
+    b->nmax = std::max(b->nmax, n);
+  }
+  // largest registers first
+  b->order.resize(count);
+  for (int r = 0; r < count; ++r) b->order[r] = r;
+  std::stable_sort(b->order.begin(), b->order.end(), [&](int x, int y) {
+    const int64_t wx = (int64_t)b->items[x].steps << b->items[x].n, wy = (int64_t)b->items[y].steps << b->items[y].n;
+    return wx > wy;
+  });
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  cudaSetDevice(ctx->device);
+  b->blocks_per_sm = batch_prepare(b->c64);
+  if (b->blocks_per_sm < 1) return fail(RSV_ERR_CUDA, "batched kernel does not fit on an SM");
+  b->grid = std::min(count, b->blocks_per_sm * ctx->num_sms);
+  b->work_stride = (int64_t)(cfg.m_max + 1) << b->nmax;
+  rsv_status st = RSV_OK;
+  auto A = [&](size_t bytes, void** p) {
+    if (st == RSV_OK) st = b->alloc(std::max<size_t>(bytes, 16), p);
+  };
+  A(sizeof(BatchItem) * count, (void**)&b->d_items);
+  A(sizeof(int) * count, (void**)&b->d_order);
+  A(sizeof(int), (void**)&b->d_next);
+  A(b->state_amps * ab, &b->d_states);
+  A(b->state_amps * ab, &b->d_init);
+  A(sizeof(double) * params.size(), (void**)&b->d_params);
+  A(sizeof(double) * vmat.size(), (void**)&b->d_vmat);
+  A(sizeof(double) * occ_doubles, (void**)&b->d_occ);
+  A(sizeof(BatchOut) * count, (void**)&b->d_out);
+  A((size_t)b->work_stride * b->grid * ab, &b->d_work);
+  if (st != RSV_OK) return st;
+  RSV_CUDA(cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking));
+  RSV_CUDA(cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming));
+  RSV_CUDA(cudaEventCreate(&b->ev0));
+  RSV_CUDA(cudaEventCreate(&b->ev1));
+  RSV_CUDA(cudaMemcpyAsync(b->d_items, b->items.data(), sizeof(BatchItem) * count, cudaMemcpyHostToDevice, b->stream));
+  RSV_CUDA(cudaMemcpyAsync(b->d_order, b->order.data(), sizeof(int) * count, cudaMemcpyHostToDevice, b->stream));
+  RSV_CUDA(cudaMemcpyAsync(b->d_init, init.data(), init.size(), cudaMemcpyHostToDevice, b->stream));
+  RSV_CUDA(cudaMemcpyAsync(b->d_params, params.data(), sizeof(double) * params.size(), cudaMemcpyHostToDevice,
+                           b->stream));
+  RSV_CUDA(cudaMemcpyAsync(b->d_vmat, vmat.data(), sizeof(double) * vmat.size(), cudaMemcpyHostToDevice, b->stream));
+  RSV_CUDA(cudaMemsetAsync(b->d_occ, 0, sizeof(double) * std::max<size_t>(occ_doubles, 1), b->stream));
+  RSV_CUDA(cudaStreamSynchronize(b->stream));
+  if (tune_m) RSV_TRY(batch_tune_krylov(b.get()));
+  RSV_TRY(batch_capture(b.get()));
+  ctx->batches.insert(b.get());
+  *out = b.release();
+  return RSV_OK;
+}
+
+rsv_status rsv_batch_run(rsv_batch* b) {
+  g_last_error.clear();
+  if (!b) return fail(RSV_ERR_INVALID_ARG, "NULL batch");
+  std::lock_guard<std::mutex> lk(b->ctx->mu);
+  cudaSetDevice(b->ctx->device);
+  b->have_out = false;
+  // ordered after the context stream's earlier work (inputs written there)
+  RSV_CUDA(cudaEventRecord(b->ev_in, b->ctx->stream));
+  RSV_CUDA(cudaStreamWaitEvent(b->stream, b->ev_in, 0));
+  RSV_CUDA(cudaEventRecord(b->ev0, b->stream));
+  RSV_CUDA(cudaGraphLaunch(b->exec, b->stream));
+  RSV_CUDA(cudaEventRecord(b->ev1, b->stream));
+  b->out.resize(b->count);
+  RSV_CUDA(cudaMemcpyAsync(b->out.data(), b->d_out, sizeof(BatchOut) * b->count, cudaMemcpyDeviceToHost, b->stream));
+  RSV_CUDA(cudaStreamSynchronize(b->stream));
+  RSV_CUDA(cudaEventElapsedTime(&b->last_ms, b->ev0, b->ev1));
+  b->have_out = true;
+  ++b->runs;
+  for (int r = 0; r < b->count; ++r)
+    if (b->out[r].status != 0)
+      return fail(RSV_ERR_NOT_CONVERGED, "register " + std::to_string(r) + ": Krylov step needed more than " +
+                                             std::to_string(b->cfg.max_substeps) + " substeps");
+  return RSV_OK;
+}
+
+rsv_status rsv_batch_state_device(const rsv_batch* b, int32_t index, void** dev_ptr, size_t* bytes) {
+  g_last_error.clear();
+  if (!b || !dev_ptr || !bytes) return fail(RSV_ERR_INVALID_ARG, "NULL argument");
+  if (index < 0 || index >= b->count) return fail(RSV_ERR_INVALID_ARG, "index out of range");
+  const BatchItem& it = b->items[index];
+  const int64_t ab = amp_bytes(b->cfg.precision);
+  *dev_ptr = static_cast<char*>(b->d_states) + it.state_off * ab;
+  *bytes = (size_t(1) << it.n) * ab;
+  return RSV_OK;
+}
+
+rsv_status rsv_batch_state(const rsv_batch* b, int32_t index, void* host_dst, size_t bytes) {
+  void* p = nullptr;
+  size_t need = 0;
+  RSV_TRY(rsv_batch_state_device(b, index, &p, &need));
+  if (!host_dst || bytes < need) return fail(RSV_ERR_INVALID_ARG, "destination too small");
+  RSV_CUDA(cudaMemcpyAsync(host_dst, p, need, cudaMemcpyDeviceToHost, b->stream));
+  RSV_CUDA(cudaStreamSynchronize(b->stream));
+  return RSV_OK;
+}
+
+rsv_status rsv_batch_occupations(const rsv_batch* b, int32_t index, double* dst, int32_t capacity_rows,
+                                 int32_t* n_rows) {
+  g_last_error.clear();
+  if (!b || !n_rows) return fail(RSV_ERR_INVALID_ARG, "NULL argument");
+  if (index < 0 || index >= b->count) return fail(RSV_ERR_INVALID_ARG, "index out of range");
+  if (!b->have_out) return fail(RSV_ERR_INVALID_ARG, "batch has not run");
+  const BatchItem& it = b->items[index];
+  *n_rows = b->out[index].rows;
+  if (dst) {
+    const int rows = std::min(capacity_rows, b->out[index].rows);
+    if (rows > 0) {
+      RSV_CUDA(cudaMemcpyAsync(dst, b->d_occ + it.occ_off, sizeof(double) * rows * it.n, cudaMemcpyDeviceToHost,
+                               b->stream));
+      RSV_CUDA(cudaStreamSynchronize(b->stream));
+    }
+  }
+  return RSV_OK;
+}
+
+rsv_status rsv_batch_stats(const rsv_batch* b, int32_t index, rsv_stats* out) {
+  g_last_error.clear();
+  if (!b || !out) return fail(RSV_ERR_INVALID_ARG, "NULL argument");
+  if (index < -1 || index >= b->count) return fail(RSV_ERR_INVALID_ARG, "index out of range");
+  std::memset(out, 0, sizeof(*out));
+  if (!b->have_out) return RSV_OK;
+  for (int r = 0; r < b->count; ++r) {
+    if (index >= 0 && r != index) continue;
+    out->steps += b->out[r].status == 0 ? b->items[r].steps : 0;
+    out->krylov_iterations += b->out[r].iterations;
+    out->substeps += b->out[r].substeps;
+    out->max_error_estimate = std::max(out->max_error_estimate, b->out[r].max_err);
+  }
+  out->seconds = b->last_ms * 1e-3;
+  out->kernel_launches = b->runs;
+  out->tile_passes = b->grid;
+  out->krylov_dim_max = b->cfg.m_max;
+  return RSV_OK;
+}
+
+void rsv_batch_destroy(rsv_batch* b) {
+  if (!b) return;
+  {
+    std::lock_guard<std::mutex> lk(b->ctx->mu);
+    b->ctx->batches.erase(b);
+  }
+  delete b;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Serving: requests are admitted by device-memory footprint; each admitted
+// solve runs on a worker thread with its own CUDA stream, so solves of
+// different requests overlap on the device.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct ServeRequest {
+  uint64_t ticket = 0;
+  std::vector<double> pos, om, de, ph;
+  std::vector<char> init;
+  rsv_problem prob{};
+  rsv_config cfg{};
+  size_t bytes = 0;
+  int state = 0;  // 0 queued, 1 running, 2 done
+  rsv_status status = RSV_OK;
+  std::string error;
+  rsv_result* result = nullptr;
+  double t_submit = 0.0, t_admit = 0.0, t_done = 0.0;
+};
+
+}  // namespace
+
+struct rsv_server {
+  rsv_ctx* ctx = nullptr;
+  int slots = 0;
+  size_t budget = 0, in_use = 0;
+  double max_bypass_s = 0.5;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<ServeRequest*> queue;
+  std::map<uint64_t, std::unique_ptr<ServeRequest>> reqs;
+  uint64_t next_ticket = 1;
+  int running = 0;
+  bool stop = false;
+  std::vector<std::thread> workers;
+  const std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
+
+  double now() const { return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count(); }
+
+  // The first queued request that fits; requests behind a head that does not
+  // fit may pass it only while it has waited less than max_bypass_s.
+  std::deque<ServeRequest*>::iterator pick() {
+    if (queue.empty()) return queue.end();
+    const size_t room = budget - in_use;
+    auto head = queue.begin();
+    if ((*head)->bytes <= room) return head;
+    if (max_bypass_s < 0.0 || now() - (*head)->t_submit >= max_bypass_s) return queue.end();
+    for (auto it = std::next(head); it != queue.end(); ++it)
+      if ((*it)->bytes <= room) return it;
+    return queue.end();
+  }
+
+  rsv_status serve(ServeRequest* r, rsv_result** out) {
+    cudaStream_t st = nullptr;
+    RSV_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    rsv_solver* s = nullptr;
+    const rsv_status c = solver_create(ctx, &r->prob, &r->cfg, st, &s);
+    if (c != RSV_OK) {
+      cudaStreamDestroy(st);
+      return c;
+    }
+    s->own_stream = true;
+    const rsv_status k = solver_step(s, s->nsteps);
+    if (k != RSV_OK) {
+      rsv_solver_destroy(s);
+      return k;
+    }
+    return make_result(s, out);
+  }
+
+  void worker() {
+    cudaSetDevice(ctx->device);
+    for (;;) {
+      ServeRequest* r = nullptr;
+      {
+        std::unique_lock<std::mutex> lk(mu);
+        // a bypass window closing changes pick(): re-check at least every 50 ms
+        while (!stop && pick() == queue.end()) cv_work.wait_for(lk, std::chrono::milliseconds(50));
+        if (stop) return;
+        auto it = pick();
+        r = *it;
+        queue.erase(it);
+        in_use += r->bytes;
+        ++running;
+        r->state = 1;
+        r->t_admit = now();
+      }
+      rsv_result* res = nullptr;
+      const rsv_status st = serve(r, &res);
+      const std::string err = st == RSV_OK ? std::string() : g_last_error;
+      {
+        std::lock_guard<std::mutex> lk(mu);
+        r->t_done = now();
+        r->status = st;
+        r->error = err;
+        r->result = res;
+        if (res) {
+          res->wait_s = r->t_admit - r->t_submit;
+          res->service_s = r->t_done - r->t_admit;
+        }
+        r->state = 2;
+        in_use -= r->bytes;
+        --running;
+      }
+      cv_done.notify_all();
+      cv_work.notify_all();
+    }
+  }
+};
+
+extern "C" {
+
+rsv_status rsv_server_create(rsv_ctx* ctx, const rsv_server_config* config, rsv_server** out) {
+  g_last_error.clear();
+  if (!ctx || !out) return fail(RSV_ERR_INVALID_ARG, "NULL argument");
+  *out = nullptr;
+  rsv_server_config cfg{};
+  if (config) cfg = *config;
+  if (cfg.reserved != 0) return fail(RSV_ERR_INVALID_ARG, "reserved must be 0");
+  if (cfg.slots == 0) cfg.slots = 4;
+  if (cfg.slots < 1 || cfg.slots > 64) return fail(RSV_ERR_INVALID_ARG, "slots must be in [1, 64]");
+  std::unique_ptr<rsv_server> srv(new rsv_server());
+  srv->ctx = ctx;
+  srv->slots = cfg.slots;
+  srv->max_bypass_s = cfg.max_bypass_s == 0.0 ? 0.5 : cfg.max_bypass_s;
+  {
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    cudaSetDevice(ctx->device);
+    size_t budget = cfg.memory_bytes;
+    const size_t arena_free = ctx->arena.cap() > 0 ? ctx->arena.cap() - ctx->arena.used() : 0;
+    if (budget == 0) {
+      if (ctx->arena.cap() > 0) {
+        budget = arena_free;
+      } else {
+        size_t fr = 0, tot = 0;
+        RSV_CUDA(cudaMemGetInfo(&fr, &tot));
+        budget = fr / 10 * 9;
+      }
+    } else if (ctx->arena.cap() > 0 && budget > arena_free) {
+      return fail(RSV_ERR_OUT_OF_MEMORY, "memory_bytes exceeds the context arena's free bytes");
+    }
+    srv->budget = budget;
+    ctx->servers.insert(srv.get());
+  }
+  rsv_server* p = srv.release();
+  for (int i = 0; i < p->slots; ++i) p->workers.emplace_back([p] { p->worker(); });
+  *out = p;
+  return RSV_OK;
+}
+
+rsv_status rsv_submit(rsv_server* srv, const rsv_problem* problem, const rsv_config* config, uint64_t* ticket) {
+  g_last_error.clear();
+  if (!srv || !config || !ticket) return fail(RSV_ERR_INVALID_ARG, "NULL argument");
+  RSV_TRY(validate_problem(problem));
+  rsv_config cfg = *config;
+  if (cfg.dt_ns < 1) return fail(RSV_ERR_INVALID_ARG, "dt_ns must be >= 1");
+  if (cfg.precision != RSV_C64 && cfg.precision != RSV_C128) return fail(RSV_ERR_INVALID_ARG, "bad precision");
+  if (cfg.m_max == 0) cfg.m_max = 30;
+  if (cfg.m_max < 2 || cfg.m_max > kMaxKrylov) return fail(RSV_ERR_INVALID_ARG, "m_max must be in [2, 64]");
+  if (cfg.obs_stride < 0) return fail(RSV_ERR_INVALID_ARG, "obs_stride must be >= 0");
+  std::unique_ptr<ServeRequest> r(new ServeRequest());
+  const int n = problem->n_atoms;
+  const size_t T = (size_t)problem->t_ns;
+  r->pos.assign(problem->positions_um, problem->positions_um + (size_t)n * problem->dim);
+  r->om.assign(problem->omega, problem->omega + (size_t)problem->omega_rows * T);
+  r->de.assign(problem->delta, problem->delta + (size_t)problem->delta_rows * T);
+  if (problem->phi_rows > 0) r->ph.assign(problem->phi, problem->phi + (size_t)problem->phi_rows * T);
+  if (problem->initial_state) {
+    const char* c = static_cast<const char*>(problem->initial_state);
+    r->init.assign(c, c + (size_t(1) << n) * amp_bytes(cfg.precision));
+  }
+  r->prob = *problem;
+  r->prob.positions_um = r->pos.data();
+  r->prob.omega = r->om.data();
+  r->prob.delta = r->de.data();
+  r->prob.phi = r->ph.empty() ? nullptr : r->ph.data();
+  r->prob.initial_state = r->init.empty() ? nullptr : r->init.data();
+  r->cfg = cfg;
+  r->bytes = solver_bytes(&r->prob, cfg);
+  std::lock_guard<std::mutex> lk(srv->mu);
+  if (r->bytes > srv->budget)
+    return fail(RSV_ERR_OUT_OF_MEMORY, "request footprint " + std::to_string(r->bytes) + " B exceeds the server's " +
+                                           std::to_string(srv->budget) + " B");
+  r->ticket = srv->next_ticket++;
+  r->t_submit = srv->now();
+  *ticket = r->ticket;
+  srv->queue.push_back(r.get());
+  srv->reqs[r->ticket] = std::move(r);
+  srv->cv_work.notify_one();
+  return RSV_OK;
+}
+
+rsv_status rsv_poll(rsv_server* srv, uint64_t ticket, int32_t timeout_ms, rsv_result** out) {
+  g_last_error.clear();
+  if (!srv || !out) return fail(RSV_ERR_INVALID_ARG, "NULL argument");
+  *out = nullptr;
+  std::unique_lock<std::mutex> lk(srv->mu);
+  auto it = srv->reqs.find(ticket);
+  if (it == srv->reqs.end()) return fail(RSV_ERR_NOT_FOUND, "unknown ticket " + std::to_string(ticket));
+  ServeRequest* r = it->second.get();
+  auto done = [&] { return r->state == 2; };
+  if (timeout_ms < 0)
+    srv->cv_done.wait(lk, done);
+  else if (timeout_ms > 0)
+    srv->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), done);
+  if (!done()) return fail(RSV_ERR_TIMEOUT, "ticket " + std::to_string(ticket) + " is still pending");
+  const rsv_status st = r->status;
+  const std::string err = r->error;
+  *out = r->result;
+  srv->reqs.erase(it);
+  if (st != RSV_OK) return fail(st, err);
+  return RSV_OK;
+}
+
+rsv_status rsv_server_load(rsv_server* srv, int32_t* queued, int32_t* running, size_t* bytes_in_use) {
+  if (!srv) return fail(RSV_ERR_INVALID_ARG, "NULL server");
+  std::lock_guard<std::mutex> lk(srv->mu);
+  if (queued) *queued = (int32_t)srv->queue.size();
+  if (running) *running = srv->running;
+  if (bytes_in_use) *bytes_in_use = srv->in_use;
+  return RSV_OK;
+}
+
+void rsv_server_destroy(rsv_server* srv) {
+  if (!srv) return;
+  {
+    std::lock_guard<std::mutex> lk(srv->mu);
+    srv->stop = true;
+    srv->queue.clear();
+  }
+  srv->cv_work.notify_all();
+  for (auto& t : srv->workers) t.join();
+  {
+    std::lock_guard<std::mutex> lk(srv->ctx->mu);
+    srv->ctx->servers.erase(srv);
+  }
+  for (auto& kv : srv->reqs)
+    if (kv.second->result) rsv_result_free(kv.second->result);
+  delete srv;
 }
 
 }  // extern "C"

@@ -1,0 +1,136 @@
+"""GPU tests of the request server (rsv_server_*, rsv_submit, rsv_poll).
+
+Requests of mixed size and precision are submitted while others run; each
+result must be the same as the same request solved alone (rsv_run on the
+same context) within the benchmark spec's tolerances (infidelity 1e-10 for
+complex128, 1e-5 for complex64; occupations 1e-10 / 1e-5), and admission must
+keep the bytes held by running solves within the server's memory.
+"""
+import threading
+import time
+
+import numpy as np
+import pytest
+
+from oracle import rydberg as O
+from paper_2510_09813_b300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+INFID_TOL = {"c128": 1e-10, "c64": 1e-5}
+OCC_TOL = {"c128": 1e-10, "c64": 1e-5}
+
+
+def api():
+    from paper_2510_09813_b300 import api as A
+    return A
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA GPU required for -m gpu tests")
+    c = api().Context(0, arena_bytes=24 << 30)
+    yield c
+    c.close()
+
+
+def requests(seed, sizes, t_lo=60, t_hi=200):
+    out = []
+    for k, n in enumerate(sizes):
+        rng = np.random.Generator(np.random.PCG64([seed, k]))
+        t_ns = int(rng.integers(t_lo, t_hi + 1))
+        prec = "c64" if k % 2 == 0 else "c128"
+        out.append((W.random_knot_problem(rng, n, t_ns), prec))
+    return out
+
+
+def test_results_alone_equal_in_mix(ctx):
+    reqs = requests(21, [14, 9, 20, 12, 17, 11, 22, 15, 8, 19, 13, 16])
+    srv = api().Server(ctx, slots=4)
+    tickets = [srv.submit(p, 10, prec, obs_stride=1) for p, prec in reqs]
+    results = [srv.poll(t, timeout_ms=-1) for t in tickets]
+    srv.close()
+    identical = 0
+    for (p, prec), r in zip(reqs, results):
+        alone = api().run(ctx, p, 10, prec, obs_stride=1)
+        a, b = alone.state().astype(np.complex128), r.state().astype(np.complex128)
+        assert O.infidelity(b, a) <= INFID_TOL[prec]
+        assert np.max(np.abs(r.occupations() - alone.occupations())) <= OCC_TOL[prec]
+        identical += int(np.array_equal(a, b))
+        w, s = r.times()
+        assert w >= 0.0 and s > 0.0
+        alone.close()
+        r.close()
+    # same kernels, same reductions: the mix changes nothing at all
+    assert identical == len(reqs)
+
+
+def test_served_result_matches_oracle(ctx):
+    rng = np.random.Generator(np.random.PCG64(77))
+    p = W.random_knot_problem(rng, 10, 150, with_phi=True)
+    srv = api().Server(ctx, slots=2)
+    t = srv.submit(p, 10, "c128", obs_stride=1)
+    r = srv.poll(t)
+    ref, occ_ref = O.evolve(p.positions, p.c6, p.t_ns, 10, p.omega, p.delta, p.phi, method="krylov", tol=1e-14)
+    assert O.infidelity(r.state(), ref) <= 1e-10
+    assert np.max(np.abs(r.occupations() - occ_ref)) <= 1e-10
+    r.close()
+    srv.close()
+
+
+def test_admission_respects_memory(ctx):
+    """A server whose memory holds about two of these solves never runs more
+    than fits; every request still completes, also the ones that waited."""
+    reqs = requests(22, [21, 21, 21, 21, 21, 21], t_lo=40, t_hi=60)
+    reqs = [(p, "c128") for p, _ in reqs]
+    one = api().footprint_bytes(21, "c128", 30)
+    srv = api().Server(ctx, slots=6, memory_bytes=int(2.5 * one), max_bypass_s=-1)
+    peak = {"bytes": 0, "running": 0}
+    stop = threading.Event()
+
+    def sample():
+        while not stop.is_set():
+            q, r, b = srv.load()
+            peak["bytes"] = max(peak["bytes"], b)
+            peak["running"] = max(peak["running"], r)
+            time.sleep(0.001)
+
+    th = threading.Thread(target=sample)
+    th.start()
+    tickets = [srv.submit(p, 10, prec) for p, prec in reqs]
+    results = [srv.poll(t) for t in tickets]
+    stop.set()
+    th.join()
+    assert peak["bytes"] <= int(2.5 * one)
+    assert 1 <= peak["running"] <= 2
+    waits = [r.times()[0] for r in results]
+    assert max(waits) > 0.0
+    for r in results:
+        r.close()
+    srv.close()
+
+
+def test_errors(ctx):
+    A = api()
+    srv = A.Server(ctx, slots=1, memory_bytes=64 << 20)
+    rng = np.random.Generator(np.random.PCG64(5))
+    big = W.random_knot_problem(rng, 22, 20)
+    with pytest.raises(A.RsvError) as e:
+        srv.submit(big, 10, "c128")
+    assert e.value.code == -2
+    with pytest.raises(A.RsvError) as e:
+        srv.poll(12345, 0)
+    assert e.value.code == -7
+    # 2000 one-ns steps cannot finish within the first poll
+    small = W.random_knot_problem(rng, 10, 2000)
+    t = srv.submit(small, 1, "c128")
+    assert srv.poll(t, 0) is None
+    r = srv.poll(t, -1)
+    assert r is not None
+    with pytest.raises(A.RsvError) as e:
+        srv.poll(t, 0)  # retired once claimed
+    assert e.value.code == -7
+    r.close()
+    srv.close()
