@@ -43,6 +43,7 @@ N_ATOMS = 28
 BATCH_M_MAX = -1  # Krylov depth autotuned on a sample of the registers
 SERVE_ARENA = 160 << 30
 SERVE_REQUESTS = 32
+SERVE_MAX_ATOMS = 20
 TRANSIENT_STEPS = 5  # steps of the Krylov space growing from |0...0> (13-19 iterations)
 DT_NS = 5
 M_MAX = 20
@@ -241,11 +242,12 @@ def batched_leg(api, W, device: int):
             "speedup_vs_one_at_a_time_c128": one_s / sec}
 
 
-def serving_leg(api, W, device: int, count: int):
-    """Replay the first `count` requests of the serving stream at their arrival
-    times: continuous batching (4 slots, mixed precision) and the plain
-    one-solve-at-a-time complex128 server (1 slot, FIFO)."""
-    reqs = W.serving_stream(seed=5, count=count)
+def serving_leg(api, W, device: int, count: int, n_hi: int):
+    """Replay the first `count` requests of the serving stream (atoms up to
+    n_hi) at their arrival times: continuous batching (4 slots, mixed
+    precision) and the plain one-solve-at-a-time complex128 server (1 slot,
+    FIFO)."""
+    reqs = W.serving_stream(seed=5, count=count, n_hi=n_hi)
     ctx = api.Context(device, arena_bytes=SERVE_ARENA)
 
     def replay(slots, force_c128):
@@ -274,7 +276,8 @@ def serving_leg(api, W, device: int, count: int):
     mixed = replay(4, False)
     fifo = replay(1, True)
     ctx.close()
-    return {"workload": SERVE_WORKLOAD, "requests": count, "continuous_batching": {"slots": 4, **mixed},
+    wl = SERVE_WORKLOAD if n_hi == 26 else SERVE_WORKLOAD.replace("U{12..26}", f"U{{12..{n_hi}}}")
+    return {"workload": wl, "requests": count, "continuous_batching": {"slots": 4, **mixed},
             "one_at_a_time_c128": {"slots": 1, **fifo}}
 
 
@@ -424,7 +427,8 @@ def ours(args):
     ctx2.close()
 
     batched = None if args.no_batch else batched_leg(api, W, local)
-    serving = None if args.serve_requests <= 0 else serving_leg(api, W, local, args.serve_requests)
+    serving = None if args.serve_requests <= 0 else serving_leg(api, W, local, args.serve_requests,
+                                                                args.serve_max_atoms)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -495,6 +499,26 @@ def profile_case(n_atoms: int):
     return 0
 
 
+def profile_batch():
+    """A small batched run for ncu captures: 24 registers of 16-18 atoms and 24
+    of 10-12, 100 ns of 8-knot pulses, complex64, m_max 30."""
+    from paper_2510_09813_b300 import api
+    from paper_2510_09813_b300 import workloads as W
+    probs = []
+    for k in range(48):
+        rng = np.random.Generator(np.random.PCG64([9, k]))
+        n = int(rng.integers(16, 19)) if k < 24 else int(rng.integers(10, 13))
+        probs.append(W.random_knot_problem(rng, n, 100))
+    ctx = api.Context(0)
+    b = api.Batch(ctx, probs, 10, "c64", m_max=30, obs_stride=0)
+    b.run()
+    b.run()
+    st = b.stats()
+    b.close()
+    print(json.dumps({"profile_batch": len(probs), "stats": st}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -505,9 +529,15 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the 512-register batched leg")
     ap.add_argument("--serve-requests", type=int, default=SERVE_REQUESTS,
                     help="requests of the serving leg (0 skips it)")
+    ap.add_argument("--serve-max-atoms", type=int, default=SERVE_MAX_ATOMS,
+                    help="largest register of the serving stream (26 = the full stream; the default keeps "
+                         "the leg within about a minute)")
     ap.add_argument("--profile-case", type=int, default=0, metavar="N",
                     help="run the small ncu case at N atoms instead of the benchmark")
+    ap.add_argument("--profile-batch", action="store_true", help="run the small batched ncu case")
     args = ap.parse_args()
+    if args.profile_batch:
+        return profile_batch()
     if args.profile_case:
         return profile_case(args.profile_case)
     if args.warmup < 3:

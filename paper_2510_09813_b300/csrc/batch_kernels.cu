@@ -485,11 +485,14 @@ cudaError_t launch_batch(const BatchArgs& a, bool c64, int grid, cudaStream_t st
 
 int batch_prepare(bool c64) {
   int nb = 0;
+  // several CTAs per SM need the shared-memory side of the L1/shared split
   if (c64) {
+    cudaFuncSetAttribute(batch_kernel<float>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     cudaFuncSetAttribute(batch_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)batch_dynamic_smem<float>());
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_kernel<float>, kThreads, batch_dynamic_smem<float>());
   } else {
+    cudaFuncSetAttribute(batch_kernel<double>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     cudaFuncSetAttribute(batch_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)batch_dynamic_smem<double>());
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_kernel<double>, kThreads, batch_dynamic_smem<double>());

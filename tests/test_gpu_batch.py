@@ -76,9 +76,10 @@ def test_batch_matches_oracle(ctx, prec, with_phi):
 
 
 def test_batch_full_sequence_and_initial_states(ctx):
-    """Full 1 us, 8-knot pulses (100 steps), random initial states, odd dt."""
+    """8-knot pulses over 301 ns with dt = 7 (43 steps, a ragged last step),
+    random initial states, occupation rows every 10 steps and at the end."""
     sizes = [6, 9, 11, 13]
-    probs = mixed_problems(12, sizes, 1000)
+    probs = mixed_problems(12, sizes, 301)
     inits = [W.random_state(50 + k, n) for k, n in enumerate(sizes)]
     b = api().Batch(ctx, probs, 7, "c128", obs_stride=10, initial_states=inits)
     b.run()
