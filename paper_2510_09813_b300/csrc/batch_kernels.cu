@@ -8,17 +8,22 @@
 // psi = |psi| sum_k u_k v_k and the occupations <n_i>. Nothing returns to the
 // host between steps.
 //
-// Matvec of one Krylov vector v (2^n amplitudes, in global memory, L2-resident
-// for the sizes this kernel serves): chunks of 2^T amplitudes (T = min(n, TB))
-// are staged in shared memory; flips of bits < T read the staged chunk, flips
-// of bits >= T read the partner chunk from global memory (coalesced). The
-// diagonal E(b) = E_hi(chunk) + sum_{q<T} w_q b_q + Q[b mod 2^T] is never
-// stored: Q is a per-register shared table, (w_q, E_hi) a per-chunk row.
-// Registers with n <= TB are one chunk: forming v_j from (u, v_{j-1}) fuses
-// into the staging, so an iteration is a single sweep.
+// Matvec of one Krylov vector (2^n amplitudes in global memory, L2-resident for
+// most of the sizes this kernel serves), in 16-byte vectors (two complex64 or
+// one complex128 amplitude) with packed FP32x2 arithmetic for complex64:
+//   - pass A walks contiguous chunks of 2^T amplitudes (T = min(n, TB)): it
+//     forms v_j while staging the chunk in shared memory, adds the diagonal
+//     E(b) = E_hi(chunk) + sum_{q<T} w_q b_q + Q[b mod 2^T] (never stored) and
+//     the flips of bits < T: the in-vector bit from the vector itself, the 8
+//     thread bits from shared memory, the 3 register bits from the thread's
+//     own vectors;
+//   - for n > TB, pass B walks strided chunks (2^(TB-h) contiguous amplitudes
+//     times every value of the h = n - TB high bits) and adds their flips.
+// Registers with n <= TB are one chunk, so an iteration is a single sweep.
 #include "kernels.h"
 #include "krylov_math.cuh"
 #include "rsv_common.cuh"
+#include "vec_ops.cuh"
 
 namespace rsv {
 
@@ -33,25 +38,26 @@ struct BatchCfg<double> {
   static constexpr int TB = 11;  // 2^11 complex128 = 32 KiB chunk
 };
 
+// dynamic shared memory: the staged chunk (2^TB amplitudes, 32 KiB) and Q
 template <typename Real>
 size_t batch_dynamic_smem() {
-  using C2 = typename CplxT<Real>::type;
-  return (sizeof(C2) + sizeof(Real)) << BatchCfg<Real>::TB;
+  return (2 * sizeof(Real) + sizeof(Real)) << BatchCfg<Real>::TB;
 }
 
 namespace {
 
+constexpr int kBK = 8;   // vectors per thread of a full chunk (2^11 vectors / 256 threads)
+constexpr int kBKK = 3;  // register bits of a full chunk
+
 template <typename Real>
 struct Shared {
-  using C2 = typename CplxT<Real>::type;
   double V[kBatchMaxAtoms][kBatchMaxAtoms];  // pair energies by bit position
   double delta[kBatchMaxAtoms];
-  Real h[kBatchMaxAtoms];                    // Omega/2
-  Real hc[kBatchMaxAtoms], hs[kBatchMaxAtoms];  // Omega/2 cos phi, Omega/2 sin phi
+  Coef cp[kBatchMaxAtoms][2];                // flip coefficient by [bit][target bit value], phase form
+  Coef cf[kMaxKrylov];                       // combine coefficients |psi| u_k, phase form
   Real w[BatchCfg<Real>::TB];
   Real ehi;
   double al[kMaxKrylov], be[kMaxKrylov + 1], ur[kMaxKrylov], ui[kMaxKrylov];
-  Real cr[kMaxKrylov], ci[kMaxKrylov];
   ChebWork cw;
   double red[(kBatchMaxAtoms + 1) * (kThreads / 32)];
   double tot[kBatchMaxAtoms + 1];
@@ -61,17 +67,6 @@ struct Shared {
   int m;
   int item;
 };
-
-__device__ __forceinline__ float2 cmul_re(float2 x, float r) { return make_float2(x.x * r, x.y * r); }
-__device__ __forceinline__ double2 cmul_re(double2 x, double r) { return make_double2(x.x * r, x.y * r); }
-
-template <typename C2, typename Real>
-__device__ __forceinline__ C2 make_c(Real re, Real im) {
-  C2 z;
-  z.x = re;
-  z.y = im;
-  return z;
-}
 
 // Per-chunk diagonal row: s.w[q] = sum_{r >= T} V_qr b_r - delta_q (q < T) and
 // s.ehi = sum_{T <= q < r} V_qr b_q b_r - sum_{q >= T} delta_q b_q for the high
@@ -96,50 +91,128 @@ __device__ void chunk_row(Shared<Real>& s, int n, int T, int64_t c, int lane) {
   }
 }
 
-// Flip term c_q(b) p of Eq. (3) with the phase: Omega/2 e^{+i phi} when bit q
-// of b is 0, Omega/2 e^{-i phi} when it is 1.
-template <typename Real, bool PHI>
-__device__ __forceinline__ void add_flip(const Shared<Real>& s, int q, bool bit, typename CplxT<Real>::type p, Real& yr,
-                                         Real& yi) {
-  if (PHI) {
-    const Real hc = s.hc[q];
-    const Real hs = bit ? -s.hs[q] : s.hs[q];
-    yr = fma(hc, p.x, fma(-hs, p.y, yr));
-    yi = fma(hc, p.y, fma(hs, p.x, yi));
-  } else {
-    const Real h = s.h[q];
-    yr = fma(h, p.x, yr);
-    yi = fma(h, p.y, yi);
+// Pass A over contiguous chunk c (see the file comment). `reduce`: this is the
+// whole vector (n <= TB), so the Lanczos sums are taken here.
+template <typename Real, bool PHI, typename Acc>
+__device__ void pass_a(Shared<Real>& s, Vec* s_x, const Real* s_q, int n, int T, int64_t c, const Vec* src,
+                       Vec* basis_j, const Vec* basis_prev, Vec* u, bool has_prev, Real a, Real sc, Real bprev,
+                       bool reduce, Acc& r0, Acc& r1, Acc& r2) {
+  constexpr int V = CplxT<Real>::kLogVec;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int vb = T - V;
+  const int kt = vb < 8 ? vb : 8;
+  const int kk = vb - kt;
+  const int keff = 1 << kk;
+  const bool active = tid < (1 << kt);
+  const int64_t vbase = c << vb;
+  if (warp == 0) chunk_row(s, n, T, c, lane);
+#pragma unroll
+  for (int k = 0; k < kBK; ++k) {
+    if (!active || k >= keff) continue;
+    const int t = tid | (k << kt);
+    const Vec uu = ldv_vec(src, vbase + t);
+    const Vec pv = has_prev ? ldv_vec(basis_prev, vbase + t) : Vec{0ull, 0ull};
+    const Vec x = form<Real>(uu, pv, a, sc, has_prev);
+    sts_vec(s_x, t, x);
+    stg_vec(basis_j, vbase + t, x);
   }
+  __syncthreads();
+  if (active) {
+    Real lin_t = s.ehi;
+    for (int j = 0; j < kt; ++j)
+      if ((tid >> j) & 1) lin_t += s.w[V + j];
+    Vec o[kBK];
+#pragma unroll
+    for (int k = 0; k < kBK; ++k) {
+      o[k] = Vec{0ull, 0ull};
+      if (k >= keff) continue;
+      Real lk = lin_t;
+#pragma unroll
+      for (int j = 0; j < kBKK; ++j)
+        if (j < kk && ((k >> j) & 1)) lk += s.w[V + kt + j];
+      const int t = tid | (k << kt);
+      const int b0 = t << V;
+      const Real e0 = lk + s_q[b0];
+      const Real e1 = V == 1 ? lk + s.w[0] + s_q[b0 + 1] : e0;
+      const Vec x = lds_vec(s_x, t);
+      o[k] = scale2<Real>(x, e0, e1);
+      if constexpr (V == 1) {
+        // amplitude bit 0: the partner is the other half of the vector
+        cmac_word<PHI>(o[k].w0, s.cp[0][0], x.w1);
+        cmac_word<PHI>(o[k].w1, s.cp[0][1], x.w0);
+      }
+    }
+    // thread bits: partners from shared memory, all K loads of one bit together
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      if (j >= kt) continue;
+      const Coef cj = s.cp[V + j][(tid >> j) & 1];
+      Vec pp[kBK];
+#pragma unroll
+      for (int k = 0; k < kBK; ++k) pp[k] = k < keff ? lds_vec(s_x, (tid | (k << kt)) ^ (1 << j)) : Vec{0ull, 0ull};
+#pragma unroll
+      for (int k = 0; k < kBK; ++k)
+        if (k < keff) cmac<Real, PHI>(o[k], cj, pp[k]);
+    }
+    // register bits: the partner is another of this thread's vectors
+#pragma unroll
+    for (int j = 0; j < kBKK; ++j) {
+      if (j >= kk) continue;
+      const int q = V + kt + j;
+#pragma unroll
+      for (int k = 0; k < kBK; ++k)
+        if (k < keff) cmac<Real, PHI>(o[k], s.cp[q][(k >> j) & 1], lds_vec(s_x, tid | ((k ^ (1 << j)) << kt)));
+    }
+#pragma unroll
+    for (int k = 0; k < kBK; ++k) {
+      if (k >= keff) continue;
+      const int t = tid | (k << kt);
+      const int64_t vg = vbase + t;
+      if (has_prev) axpy<Real>(o[k], -bprev, ldv_vec(basis_prev, vg));  // this thread read it while staging
+      stg_vec(u, vg, o[k]);
+      if (reduce) reduce_vec<Real>(lds_vec(s_x, t), o[k], r0, r1, r2);
+    }
+  }
+  __syncthreads();
 }
 
-// Diagonal and flips of bits q < T of the amplitude at chunk-local index blo
-// of a contiguous chunk staged in s_x; lin = sum_{q<T} w_q b_q.
-template <typename Real, bool PHI>
-__device__ __forceinline__ typename CplxT<Real>::type apply_low(const Shared<Real>& s,
-                                                                 const typename CplxT<Real>::type* s_x,
-                                                                 const Real* s_q, int T, int blo, Real lin) {
-  using C2 = typename CplxT<Real>::type;
-  const C2 x = s_x[blo];
-  const Real e = s.ehi + lin + s_q[blo];
-  Real yr = e * x.x, yi = e * x.y;
-  for (int q = 0; q < T; ++q) add_flip<Real, PHI>(s, q, (blo >> q) & 1, s_x[blo ^ (1 << q)], yr, yi);
-  return make_c<C2>(yr, yi);
-}
-
-template <typename Acc, typename Real>
-__device__ __forceinline__ void acc_dot3(Acc& r0, Acc& r1, Acc& r2, Real xr, Real xi, Real yr, Real yi) {
-  if constexpr (sizeof(Real) == 4) {
-    r0.add(fmaf(xi, yi, xr * yr));
-    r1.add(fmaf(yi, yi, yr * yr));
-    r2.add(fmaf(xi, xi, xr * xr));
-  } else {
-    r0.dot(xr, yr);
-    r0.dot(xi, yi);
-    r1.dot(yr, yr);
-    r1.dot(yi, yi);
-    r2.dot(xr, xr);
-    r2.dot(xi, xi);
+// Pass B (n > TB): flips of the h = n - TB high bits over strided chunks; adds
+// them to u and takes the Lanczos sums.
+template <typename Real, bool PHI, typename Acc>
+__device__ void pass_b(Shared<Real>& s, Vec* s_x, int n, const Vec* basis_j, Vec* u, Acc& r0, Acc& r1, Acc& r2) {
+  constexpr int TB = BatchCfg<Real>::TB;
+  constexpr int V = CplxT<Real>::kLogVec;
+  constexpr int VB = TB - V;               // vector bits of a chunk (11)
+  const int tid = threadIdx.x;
+  const int h = n - TB;                    // 1 .. kBatchMaxAtoms - TB
+  const int cbv = VB - h;                  // contiguous vector bits of a segment
+  const int lowmask = (1 << cbv) - 1;
+  const int64_t nsc = int64_t(1) << h;
+  for (int64_t g = 0; g < nsc; ++g) {
+    Vec x[kBK];
+    int64_t vidx[kBK];
+#pragma unroll
+    for (int k = 0; k < kBK; ++k) {
+      const int t = tid | (k << 8);
+      vidx[k] = ((int64_t)(t >> cbv) << VB) | (g << cbv) | (t & lowmask);
+      x[k] = ldv_vec(basis_j, vidx[k]);
+      sts_vec(s_x, t, x[k]);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kBK; ++k) {
+      const int t = tid | (k << 8);
+      Vec y = ldv_vec(u, vidx[k]);
+#pragma unroll
+      for (int r = 0; r < kBatchMaxAtoms - 11 + 1; ++r) {
+        if (r >= h) break;
+        const int tb = cbv + r;  // vector-index bit of amplitude bit TB + r
+        cmac<Real, PHI>(y, s.cp[TB + r][(t >> tb) & 1], lds_vec(s_x, t ^ (1 << tb)));
+      }
+      stg_vec(u, vidx[k], y);
+      reduce_vec<Real>(x[k], y, r0, r1, r2);
+    }
+    __syncthreads();
   }
 }
 
@@ -147,155 +220,84 @@ __device__ __forceinline__ void acc_dot3(Acc& r0, Acc& r1, Acc& r2, Real xr, Rea
 //   v_j = (u - a v_{j-1}) * sc (j > 0) or psi * sc (j = 0), written to basis[j];
 //   u   = H v_j - bprev v_{j-1};
 //   Re<v_j, u>, |u|^2, |v_j|^2 -> s.tot[0..2].
-// Pass A walks contiguous chunks of 2^T amplitudes: it forms v_j while staging
-// it, then applies the diagonal and the flips of bits < T. For n > T, pass B
-// walks strided chunks (2^cb contiguous amplitudes times every value of the
-// h = n - T high bits, cb = T - h) staged from v_j and adds the flips of the
-// high bits to u. Every global access is a coalesced run of the chunk layout.
 template <typename Real, bool PHI>
-__device__ void lanczos_iteration(Shared<Real>& s, typename CplxT<Real>::type* s_x, const Real* s_q, int n, int T,
-                                  const typename CplxT<Real>::type* src, typename CplxT<Real>::type* basis_j,
-                                  const typename CplxT<Real>::type* basis_prev, typename CplxT<Real>::type* u,
-                                  int j, Real a, Real sc, Real bprev) {
-  using C2 = typename CplxT<Real>::type;
+__device__ void lanczos_iteration(Shared<Real>& s, Vec* s_x, const Real* s_q, int n, int T, const Vec* src,
+                                  Vec* basis_j, const Vec* basis_prev, Vec* u, int j, Real a, Real sc, Real bprev) {
   using Acc = typename AccFor<Real>::type;
-  constexpr int KMAX = 1 << (BatchCfg<Real>::TB - 8);
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int64_t D = int64_t(1) << n;
-  const int chunk = 1 << T;
-  const int per = chunk >= kThreads ? chunk / kThreads : 1;
-  const bool active = tid < chunk;
-  const int64_t nch = D >> T;
+  const int64_t nch = int64_t(1) << (n - T);
   Acc r0, r1, r2;
-  for (int64_t c = 0; c < nch; ++c) {
-    const int64_t base = c << T;
-    if (warp == 0) chunk_row(s, n, T, c, lane);
-    if (active) {
-#pragma unroll
-      for (int k = 0; k < KMAX; ++k) {
-        if (k >= per) break;
-        const int blo = tid + k * kThreads;
-        const C2 x = src[base + blo];
-        C2 v;
-        if (j == 0) {
-          v = cmul_re(x, sc);
-        } else {
-          const C2 p = basis_prev[base + blo];
-          v = make_c<C2>((x.x - a * p.x) * sc, (x.y - a * p.y) * sc);
-        }
-        s_x[blo] = v;
-        basis_j[base + blo] = v;
-      }
-    }
-    __syncthreads();
-    if (active) {
-      Real lin_t = 0;
-      for (int q = 0; q < T && q < 8; ++q)
-        if ((tid >> q) & 1) lin_t += s.w[q];
-#pragma unroll
-      for (int k = 0; k < KMAX; ++k) {
-        if (k >= per) break;
-        const int blo = tid + k * kThreads;
-        Real lin = lin_t;
-        for (int q = 8; q < T; ++q)
-          if ((k >> (q - 8)) & 1) lin += s.w[q];
-        C2 y = apply_low<Real, PHI>(s, s_x, s_q, T, blo, lin);
-        if (j > 0) {
-          // v_{j-1} again (this thread read the same words while staging)
-          const C2 p = basis_prev[base + blo];
-          y.x = fma(-bprev, p.x, y.x);
-          y.y = fma(-bprev, p.y, y.y);
-        }
-        u[base + blo] = y;
-        if (nch == 1) {
-          const C2 x = s_x[blo];
-          acc_dot3(r0, r1, r2, x.x, x.y, y.x, y.y);
-        }
-      }
-    }
-    __syncthreads();
-  }
-  if (nch > 1) {
-    const int h = n - T, cb = T - h;
-    const int64_t nsc = int64_t(1) << (T - cb);
-    const int lowmask = (1 << cb) - 1;
-    for (int64_t g = 0; g < nsc; ++g) {
-#pragma unroll
-      for (int k = 0; k < KMAX; ++k) {
-        if (k >= per) break;
-        const int idx = tid + k * kThreads;
-        const int64_t b = ((int64_t)(idx >> cb) << T) | (g << cb) | (idx & lowmask);
-        s_x[idx] = basis_j[b];
-      }
-      __syncthreads();
-#pragma unroll
-      for (int k = 0; k < KMAX; ++k) {
-        if (k >= per) break;
-        const int idx = tid + k * kThreads;
-        const int64_t b = ((int64_t)(idx >> cb) << T) | (g << cb) | (idx & lowmask);
-        C2 y = u[b];
-        for (int q = T; q < n; ++q) {
-          const int bit = cb + (q - T);
-          add_flip<Real, PHI>(s, q, (idx >> bit) & 1, s_x[idx ^ (1 << bit)], y.x, y.y);
-        }
-        u[b] = y;
-        const C2 x = s_x[idx];
-        acc_dot3(r0, r1, r2, x.x, x.y, y.x, y.y);
-      }
-      __syncthreads();
-    }
-  }
+  for (int64_t c = 0; c < nch; ++c)
+    pass_a<Real, PHI>(s, s_x, s_q, n, T, c, src, basis_j, basis_prev, u, j > 0, a, sc, bprev, nch == 1, r0, r1, r2);
+  if (nch > 1) pass_b<Real, PHI>(s, s_x, n, basis_j, u, r0, r1, r2);
   Acc acc[3] = {r0, r1, r2};
   block_reduce_write<3>(acc, s.red, s.tot, 3);
 }
 
-// psi = sum_{k<m} (cr_k + i ci_k) basis_k (combine) or psi as is (observe),
-// with |psi|^2 -> s.tot[0] and sum_b |psi_b|^2 b_q -> s.tot[1 + q].
+// psi = sum_{k<m} cf_k basis_k (combine) or psi as is (observe), with
+// |psi|^2 -> s.tot[0] and sum_b |psi_b|^2 b_q -> s.tot[1 + q]. Products are
+// exact (TwoProduct) and sums compensated.
 template <typename Real>
-__device__ void combine_observe(Shared<Real>& s, int n, int T, typename CplxT<Real>::type* psi,
-                                const typename CplxT<Real>::type* basis, int64_t stride, int m, bool combine) {
-  using C2 = typename CplxT<Real>::type;
+__device__ void combine_observe(Shared<Real>& s, int n, int T, Vec* psi, const Vec* basis, int64_t vstride, int m,
+                                bool combine) {
   using Acc = typename AccFor<Real>::type;
-  constexpr int KB = BatchCfg<Real>::TB - 8;
-  constexpr int HB = kBatchMaxAtoms - 8;
+  constexpr int V = CplxT<Real>::kLogVec;
+  constexpr int HB = kBatchMaxAtoms - 8 - V;  // chunk-index bits at most
   const int tid = threadIdx.x;
-  const int64_t D = int64_t(1) << n;
-  const int chunk = 1 << T;
-  const int per = chunk >= kThreads ? chunk / kThreads : 1;
-  const bool active = tid < chunk;
-  const int64_t nch = D >> T;
-  Acc tot, reg[KB > 0 ? KB : 1], hi[HB];
+  const int vb = T - V;
+  const int kt = vb < 8 ? vb : 8;
+  const int kk = vb - kt;
+  const int keff = 1 << kk;
+  const bool active = tid < (1 << kt);
+  const int64_t nch = int64_t(1) << (n - T);
+  Acc tot, lane_acc, reg[kBKK], hi[HB];
   if (active) {
     for (int64_t c = 0; c < nch; ++c) {
       Acc ct;
-      for (int k = 0; k < per; ++k) {
-        const int64_t b = (c << T) + tid + k * kThreads;
-        C2 x;
+#pragma unroll
+      for (int k = 0; k < kBK; ++k) {
+        if (k >= keff) continue;
+        const int64_t vg = (c << vb) + (tid | (k << kt));
+        Vec x;
         if (combine) {
-          Real xr = 0, xi = 0;
-          for (int i = 0; i < m; ++i) {
-            const C2 v = basis[i * stride + b];
-            const Real cr = s.cr[i], ci = s.ci[i];
-            xr = fma(cr, v.x, fma(-ci, v.y, xr));
-            xi = fma(cr, v.y, fma(ci, v.x, xi));
+          x = Vec{0ull, 0ull};
+          for (int i0 = 0; i0 < m; i0 += 4) {
+            Vec bv[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+              if (i0 + q < m) bv[q] = ldv_vec(basis, (int64_t)(i0 + q) * vstride + vg);
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+              if (i0 + q < m) cmac<Real, true>(x, s.cf[i0 + q], bv[q]);
           }
-          x = make_c<C2>(xr, xi);
-          psi[b] = x;
+          stg_vec(psi, vg, x);
         } else {
-          x = psi[b];
+          x = ldv_vec(psi, vg);
         }
         Acc pv;
-        pv.dot(x.x, x.x);
-        pv.dot(x.y, x.y);
+        if constexpr (V == 1) {
+          float re0, im0, re1, im1;
+          f2_unpack(x.w0, re0, im0);
+          f2_unpack(x.w1, re1, im1);
+          Acc p1;
+          pv.dot(re0, re0);
+          pv.dot(im0, im0);
+          p1.dot(re1, re1);
+          p1.dot(im1, im1);
+          lane_acc.merge_acc(p1);
+          pv.merge_acc(p1);
+        } else {
+          pv.dot(dbl(x.w0), dbl(x.w0));
+          pv.dot(dbl(x.w1), dbl(x.w1));
+        }
         ct.merge_acc(pv);
 #pragma unroll
-        for (int r = 0; r < KB; ++r)
+        for (int r = 0; r < kBKK; ++r)
           if ((k >> r) & 1) reg[r].merge_acc(pv);
       }
       tot.merge_acc(ct);
 #pragma unroll
-      for (int h = 0; h < HB; ++h)
-        if (T + h < n && ((c >> h) & 1)) hi[h].merge_acc(ct);
+      for (int hb = 0; hb < HB; ++hb)
+        if (T + hb < n && ((c >> hb) & 1)) hi[hb].merge_acc(ct);
     }
   }
   Acc out[kBatchMaxAtoms + 1];
@@ -303,16 +305,18 @@ __device__ void combine_observe(Shared<Real>& s, int n, int T, typename CplxT<Re
 #pragma unroll
   for (int q = 0; q < kBatchMaxAtoms; ++q) {
     if (q >= n) continue;
-    if (q < 8) {
-      if ((tid >> q) & 1) out[1 + q] = tot;
+    if (q < V) {
+      out[1 + q] = lane_acc;
+    } else if (q < V + kt) {
+      if ((tid >> (q - V)) & 1) out[1 + q] = tot;
     } else if (q < T) {
 #pragma unroll
-      for (int r = 0; r < KB; ++r)
-        if (r == q - 8) out[1 + q] = reg[r];
+      for (int r = 0; r < kBKK; ++r)
+        if (r == q - V - kt) out[1 + q] = reg[r];
     } else {
 #pragma unroll
-      for (int h = 0; h < HB; ++h)
-        if (h == q - T) out[1 + q] = hi[h];
+      for (int hb = 0; hb < HB; ++hb)
+        if (hb == q - T) out[1 + q] = hi[hb];
     }
   }
   block_reduce_write<kBatchMaxAtoms + 1>(out, s.red, s.tot, n + 1);
@@ -322,15 +326,15 @@ __device__ void combine_observe(Shared<Real>& s, int n, int T, typename CplxT<Re
 
 template <typename Real>
 __global__ void __launch_bounds__(kThreads, 2) batch_kernel(const BatchArgs A) {
-  using C2 = typename CplxT<Real>::type;
   constexpr int TB = BatchCfg<Real>::TB;
+  constexpr int V = CplxT<Real>::kLogVec;
   extern __shared__ __align__(16) unsigned char dyn[];
-  C2* s_x = reinterpret_cast<C2*>(dyn);
-  Real* s_q = reinterpret_cast<Real*>(dyn + (sizeof(C2) << TB));
+  Vec* s_x = reinterpret_cast<Vec*>(dyn);
+  Real* s_q = reinterpret_cast<Real*>(dyn + (2 * sizeof(Real) << TB));
   __shared__ Shared<Real> s;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  C2* states = reinterpret_cast<C2*>(A.states);
-  C2* work = reinterpret_cast<C2*>(A.work) + (int64_t)blockIdx.x * A.work_stride;
+  Vec* states = reinterpret_cast<Vec*>(A.states);
+  Vec* work = reinterpret_cast<Vec*>(A.work) + (int64_t)blockIdx.x * (A.work_stride >> V);
 
   for (;;) {
     if (tid == 0) s.item = atomicAdd(A.next, 1);
@@ -340,11 +344,11 @@ __global__ void __launch_bounds__(kThreads, 2) batch_kernel(const BatchArgs A) {
     const BatchItem it = A.items[A.order[qi]];
     const int n = it.n;
     const int T = n < TB ? n : TB;
-    const int64_t D = int64_t(1) << n;
-    C2* psi = states + it.state_off;
-    C2* u = work + (int64_t)A.m_max * D;
-    const double* V = A.vmat + it.vmat_off;
-    for (int i = tid; i < n * n; i += kThreads) s.V[i / n][i % n] = V[i];
+    const int64_t DV = (int64_t(1) << n) >> V;  // vectors per Krylov vector
+    Vec* psi = states + (it.state_off >> V);
+    Vec* u = work + (int64_t)A.m_max * DV;
+    const double* Vm = A.vmat + it.vmat_off;
+    for (int i = tid; i < n * n; i += kThreads) s.V[i / n][i % n] = Vm[i];
     __syncthreads();
     // Q[t] = sum_{q<r<T} V_qr t_q t_r over the low bits of b (FP64, rounded once)
     for (int t = tid; t < (1 << T); t += kThreads) {
@@ -368,15 +372,17 @@ __global__ void __launch_bounds__(kThreads, 2) batch_kernel(const BatchArgs A) {
     int64_t iters = 0, subs = 0;
     double max_err = 0.0;
     int status = 0;
-    for (int step = 0; step < it.steps && status == 0; ++step) {
+    const int steps = A.step_limit > 0 && A.step_limit < it.steps ? A.step_limit : it.steps;
+    for (int step = 0; step < steps && status == 0; ++step) {
       const double* P = A.params + it.param_off + (int64_t)step * (1 + 3 * n);
       __syncthreads();
       if (tid < n) {
+        // target bit 0: <0|h|1> = Omega/2 e^{+i phi}; target bit 1: <1|h|0> = Omega/2 e^{-i phi}
         const double h = 0.5 * P[1 + tid];
         const double ph = it.has_phi ? P[1 + 2 * n + tid] : 0.0;
-        s.h[tid] = (Real)h;
-        s.hc[tid] = (Real)(h * cos(ph));
-        s.hs[tid] = (Real)(h * sin(ph));
+        const double cs = h * cos(ph), sn = h * sin(ph);
+        s.cp[tid][0] = make_coef<Real, true>((Real)cs, (Real)sn);
+        s.cp[tid][1] = make_coef<Real, true>((Real)cs, (Real)(-sn));
         s.delta[tid] = P[1 + n + tid];
       }
       if (tid == 0) s.tau = P[0];
@@ -389,9 +395,9 @@ __global__ void __launch_bounds__(kThreads, 2) batch_kernel(const BatchArgs A) {
         double a = 0.0, sc = 1.0 / b0, bprev = 0.0;
         int m = 0;
         for (int j = 0; j < A.m_max; ++j) {
-          C2* bj = work + (int64_t)j * D;
-          const C2* bp = j > 0 ? work + (int64_t)(j - 1) * D : nullptr;
-          const C2* src = j == 0 ? psi : u;
+          Vec* bj = work + (int64_t)j * DV;
+          const Vec* bp = j > 0 ? work + (int64_t)(j - 1) * DV : nullptr;
+          const Vec* src = j == 0 ? psi : u;
           if (it.has_phi)
             lanczos_iteration<Real, true>(s, s_x, s_q, n, T, src, bj, bp, u, j, (Real)a, (Real)sc, (Real)bprev);
           else
@@ -417,10 +423,8 @@ __global__ void __launch_bounds__(kThreads, 2) batch_kernel(const BatchArgs A) {
             const KrylovDecision d = krylov_decide(s.al, s.be, mk, ls.vanished ? 0.0 : beta, tau_rem, breakdown,
                                                    check, A.m_max, A.tol, s.ur, s.ui, s.cw);
             if (d.status != kContinue) {
-              for (int i = lane; i < mk; i += 32) {
-                s.cr[i] = (Real)(b0 * s.ur[i]);
-                s.ci[i] = (Real)(b0 * s.ui[i]);
-              }
+              for (int i = lane; i < mk; i += 32)
+                s.cf[i] = make_coef<Real, true>((Real)(b0 * s.ur[i]), (Real)(b0 * s.ui[i]));
             }
             if (lane == 0) {
               s.m = mk;
@@ -446,7 +450,7 @@ __global__ void __launch_bounds__(kThreads, 2) batch_kernel(const BatchArgs A) {
         last_m = m;
         double rem = tau_rem - take;
         if (st == kDone || rem <= 1e-14 * tau_rem) rem = 0.0;
-        combine_observe<Real>(s, n, T, psi, work, D, m, true);
+        combine_observe<Real>(s, n, T, psi, work, DV, m, true);
         norm2 = s.tot[0];
         tau_rem = rem;
         if (tau_rem > 0.0) {
@@ -459,7 +463,7 @@ __global__ void __launch_bounds__(kThreads, 2) batch_kernel(const BatchArgs A) {
         }
       }
       const int done = step + 1;
-      if ((it.obs_stride > 0 && done % it.obs_stride == 0) || done == it.steps) record(row++);
+      if ((it.obs_stride > 0 && done % it.obs_stride == 0) || done == steps) record(row++);
     }
     if (tid == 0) {
       BatchOut o;

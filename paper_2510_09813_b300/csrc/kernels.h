@@ -142,6 +142,7 @@ struct BatchArgs {
   int64_t work_stride;
   int m_max;
   int max_substeps;
+  int step_limit;        // > 0: stop every register after this many steps (autotuner samples)
   double tol;
   double breakdown;
 };

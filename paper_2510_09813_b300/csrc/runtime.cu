@@ -1532,6 +1532,7 @@ struct rsv_batch {
     a.work_stride = work_stride;
     a.m_max = cfg.m_max;
     a.max_substeps = cfg.max_substeps;
+    a.step_limit = 0;
     a.tol = cfg.krylov_tol;
     a.breakdown = 1e-13;
     return a;
@@ -1541,10 +1542,11 @@ struct rsv_batch {
 namespace {
 
 constexpr int kBatchTuneMax = 40;
+constexpr int kBatchTuneSteps = 10;  // steps of each sampled register per candidate
 
 // Krylov-depth autotuner of a batch: evolves a sample of the registers (spread
-// over the largest-first order) with each candidate m_max and keeps the
-// fastest. A larger m_max means fewer substeps but more FP64 exponentials per
+// over the largest-first order) over their first kBatchTuneSteps steps with
+// each candidate m_max and keeps the fastest. A larger m_max means fewer substeps but more FP64 exponentials per
 // step and a larger workspace; the best value depends on the registers'
 // spectra and time steps. The workspace is then shrunk to the chosen depth.
 rsv_status batch_tune_krylov(rsv_batch* b) {
@@ -1563,6 +1565,7 @@ rsv_status batch_tune_krylov(rsv_batch* b) {
     a.order = d_sample;
     a.count = ns;
     a.m_max = cand[c < 0 ? 0 : c];  // c = -1: warm-up launch
+    a.step_limit = kBatchTuneSteps;
     RSV_CUDA(cudaMemcpyAsync(b->d_states, b->d_init, sbytes, cudaMemcpyDeviceToDevice, b->stream));
     RSV_CUDA(cudaMemsetAsync(b->d_next, 0, sizeof(int), b->stream));
     RSV_CUDA(cudaEventRecord(b->ev0, b->stream));
