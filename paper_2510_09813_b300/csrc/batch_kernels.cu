@@ -49,6 +49,48 @@ namespace {
 constexpr int kBK = 8;   // vectors per thread of a full chunk (2^11 vectors / 256 threads)
 constexpr int kBKK = 3;  // register bits of a full chunk
 
+// ---- thread-block cluster helpers (distributed shared memory) ----
+__device__ __forceinline__ unsigned cluster_rank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+// Every thread of every CTA of the cluster; release/acquire at cluster scope
+// (shared and global memory written before it are visible after it).
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+}
+// Address of `p` (this CTA's shared memory) in the shared memory of cluster rank r.
+__device__ __forceinline__ uint32_t cluster_addr(const void* p, unsigned r) {
+  uint32_t out;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(out) : "r"(smem_u32(p)), "r"(r));
+  return out;
+}
+__device__ __forceinline__ void st_cluster(uint32_t a, double v) {
+  asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(a), "d"(v) : "memory");
+}
+__device__ __forceinline__ void st_cluster(uint32_t a, int v) {
+  asm volatile("st.shared::cluster.s32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+__device__ __forceinline__ void st_cluster(uint32_t a, unsigned long long v) {
+  asm volatile("st.shared::cluster.u64 [%0], %1;" ::"r"(a), "l"(v) : "memory");
+}
+template <typename T>
+__device__ __forceinline__ void bcast(T* local_field, T v, unsigned ncl) {
+  for (unsigned r = 0; r < ncl; ++r) st_cluster(cluster_addr(local_field, r), v);
+}
+
+// Loads of vectors another CTA of the cluster may have written: through L2
+// (the cluster barrier orders the writes; L1 holds no stale copy).
+template <bool COOP>
+__device__ __forceinline__ Vec ld_vec(const void* base, int64_t idx) {
+  if (COOP) {
+    const ulonglong2 v = __ldcg(reinterpret_cast<const ulonglong2*>(base) + idx);
+    return Vec{v.x, v.y};
+  }
+  return ldv_vec(base, idx);
+}
+
 template <typename Real>
 struct Shared {
   double V[kBatchMaxAtoms][kBatchMaxAtoms];  // pair energies by bit position
@@ -61,6 +103,7 @@ struct Shared {
   ChebWork cw;
   double red[(kBatchMaxAtoms + 1) * (kThreads / 32)];
   double tot[kBatchMaxAtoms + 1];
+  double cpart[kBatchCluster][kBatchMaxAtoms + 1];  // cluster rank 0: the CTAs' partial sums
   double tau;
   double tau_take, err, alpha, beta;
   int status;
@@ -93,7 +136,7 @@ __device__ void chunk_row(Shared<Real>& s, int n, int T, int64_t c, int lane) {
 
 // Pass A over contiguous chunk c (see the file comment). `reduce`: this is the
 // whole vector (n <= TB), so the Lanczos sums are taken here.
-template <typename Real, bool PHI, typename Acc>
+template <typename Real, bool PHI, bool COOP, typename Acc>
 __device__ void pass_a(Shared<Real>& s, Vec* s_x, const Real* s_q, int n, int T, int64_t c, const Vec* src,
                        Vec* basis_j, const Vec* basis_prev, Vec* u, bool has_prev, Real a, Real sc, Real bprev,
                        bool reduce, Acc& r0, Acc& r1, Acc& r2) {
@@ -110,8 +153,8 @@ __device__ void pass_a(Shared<Real>& s, Vec* s_x, const Real* s_q, int n, int T,
   for (int k = 0; k < kBK; ++k) {
     if (!active || k >= keff) continue;
     const int t = tid | (k << kt);
-    const Vec uu = ldv_vec(src, vbase + t);
-    const Vec pv = has_prev ? ldv_vec(basis_prev, vbase + t) : Vec{0ull, 0ull};
+    const Vec uu = ld_vec<COOP>(src, vbase + t);
+    const Vec pv = has_prev ? ld_vec<COOP>(basis_prev, vbase + t) : Vec{0ull, 0ull};
     const Vec x = form<Real>(uu, pv, a, sc, has_prev);
     sts_vec(s_x, t, x);
     stg_vec(basis_j, vbase + t, x);
@@ -168,7 +211,7 @@ __device__ void pass_a(Shared<Real>& s, Vec* s_x, const Real* s_q, int n, int T,
       if (k >= keff) continue;
       const int t = tid | (k << kt);
       const int64_t vg = vbase + t;
-      if (has_prev) axpy<Real>(o[k], -bprev, ldv_vec(basis_prev, vg));  // this thread read it while staging
+      if (has_prev) axpy<Real>(o[k], -bprev, ld_vec<COOP>(basis_prev, vg));  // this thread read it while staging
       stg_vec(u, vg, o[k]);
       if (reduce) reduce_vec<Real>(lds_vec(s_x, t), o[k], r0, r1, r2);
     }
@@ -178,8 +221,9 @@ __device__ void pass_a(Shared<Real>& s, Vec* s_x, const Real* s_q, int n, int T,
 
 // Pass B (n > TB): flips of the h = n - TB high bits over strided chunks; adds
 // them to u and takes the Lanczos sums.
-template <typename Real, bool PHI, typename Acc>
-__device__ void pass_b(Shared<Real>& s, Vec* s_x, int n, const Vec* basis_j, Vec* u, Acc& r0, Acc& r1, Acc& r2) {
+template <typename Real, bool PHI, bool COOP, typename Acc>
+__device__ void pass_b(Shared<Real>& s, Vec* s_x, int n, const Vec* basis_j, Vec* u, unsigned g0, unsigned gstep,
+                       Acc& r0, Acc& r1, Acc& r2) {
   constexpr int TB = BatchCfg<Real>::TB;
   constexpr int V = CplxT<Real>::kLogVec;
   constexpr int VB = TB - V;               // vector bits of a chunk (11)
@@ -188,21 +232,21 @@ __device__ void pass_b(Shared<Real>& s, Vec* s_x, int n, const Vec* basis_j, Vec
   const int cbv = VB - h;                  // contiguous vector bits of a segment
   const int lowmask = (1 << cbv) - 1;
   const int64_t nsc = int64_t(1) << h;
-  for (int64_t g = 0; g < nsc; ++g) {
+  for (int64_t g = g0; g < nsc; g += gstep) {
     Vec x[kBK];
     int64_t vidx[kBK];
 #pragma unroll
     for (int k = 0; k < kBK; ++k) {
       const int t = tid | (k << 8);
       vidx[k] = ((int64_t)(t >> cbv) << VB) | (g << cbv) | (t & lowmask);
-      x[k] = ldv_vec(basis_j, vidx[k]);
+      x[k] = ld_vec<COOP>(basis_j, vidx[k]);
       sts_vec(s_x, t, x[k]);
     }
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < kBK; ++k) {
       const int t = tid | (k << 8);
-      Vec y = ldv_vec(u, vidx[k]);
+      Vec y = ld_vec<COOP>(u, vidx[k]);
 #pragma unroll
       for (int r = 0; r < kBatchMaxAtoms - 11 + 1; ++r) {
         if (r >= h) break;
@@ -220,15 +264,20 @@ __device__ void pass_b(Shared<Real>& s, Vec* s_x, int n, const Vec* basis_j, Vec
 //   v_j = (u - a v_{j-1}) * sc (j > 0) or psi * sc (j = 0), written to basis[j];
 //   u   = H v_j - bprev v_{j-1};
 //   Re<v_j, u>, |u|^2, |v_j|^2 -> s.tot[0..2].
-template <typename Real, bool PHI>
+template <typename Real, bool PHI, bool COOP>
 __device__ void lanczos_iteration(Shared<Real>& s, Vec* s_x, const Real* s_q, int n, int T, const Vec* src,
-                                  Vec* basis_j, const Vec* basis_prev, Vec* u, int j, Real a, Real sc, Real bprev) {
+                                  Vec* basis_j, const Vec* basis_prev, Vec* u, int j, Real a, Real sc, Real bprev,
+                                  unsigned rank, unsigned ncl) {
   using Acc = typename AccFor<Real>::type;
   const int64_t nch = int64_t(1) << (n - T);
   Acc r0, r1, r2;
-  for (int64_t c = 0; c < nch; ++c)
-    pass_a<Real, PHI>(s, s_x, s_q, n, T, c, src, basis_j, basis_prev, u, j > 0, a, sc, bprev, nch == 1, r0, r1, r2);
-  if (nch > 1) pass_b<Real, PHI>(s, s_x, n, basis_j, u, r0, r1, r2);
+  for (int64_t c = rank; c < nch; c += ncl)
+    pass_a<Real, PHI, COOP>(s, s_x, s_q, n, T, c, src, basis_j, basis_prev, u, j > 0, a, sc, bprev, nch == 1, r0,
+                            r1, r2);
+  if (nch > 1) {
+    if (COOP) cluster_sync();  // every chunk of v_j and of the partial u is written
+    pass_b<Real, PHI, COOP>(s, s_x, n, basis_j, u, rank, ncl, r0, r1, r2);
+  }
   Acc acc[3] = {r0, r1, r2};
   block_reduce_write<3>(acc, s.red, s.tot, 3);
 }
@@ -236,9 +285,9 @@ __device__ void lanczos_iteration(Shared<Real>& s, Vec* s_x, const Real* s_q, in
 // psi = sum_{k<m} cf_k basis_k (combine) or psi as is (observe), with
 // |psi|^2 -> s.tot[0] and sum_b |psi_b|^2 b_q -> s.tot[1 + q]. Products are
 // exact (TwoProduct) and sums compensated.
-template <typename Real>
+template <typename Real, bool COOP>
 __device__ void combine_observe(Shared<Real>& s, int n, int T, Vec* psi, const Vec* basis, int64_t vstride, int m,
-                                bool combine) {
+                                bool combine, unsigned rank, unsigned ncl) {
   using Acc = typename AccFor<Real>::type;
   constexpr int V = CplxT<Real>::kLogVec;
   constexpr int HB = kBatchMaxAtoms - 8 - V;  // chunk-index bits at most
@@ -251,7 +300,7 @@ __device__ void combine_observe(Shared<Real>& s, int n, int T, Vec* psi, const V
   const int64_t nch = int64_t(1) << (n - T);
   Acc tot, lane_acc, reg[kBKK], hi[HB];
   if (active) {
-    for (int64_t c = 0; c < nch; ++c) {
+    for (int64_t c = rank; c < nch; c += ncl) {
       Acc ct;
 #pragma unroll
       for (int k = 0; k < kBK; ++k) {
@@ -264,14 +313,14 @@ __device__ void combine_observe(Shared<Real>& s, int n, int T, Vec* psi, const V
             Vec bv[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q)
-              if (i0 + q < m) bv[q] = ldv_vec(basis, (int64_t)(i0 + q) * vstride + vg);
+              if (i0 + q < m) bv[q] = ld_vec<COOP>(basis, (int64_t)(i0 + q) * vstride + vg);
 #pragma unroll
             for (int q = 0; q < 4; ++q)
               if (i0 + q < m) cmac<Real, true>(x, s.cf[i0 + q], bv[q]);
           }
           stg_vec(psi, vg, x);
         } else {
-          x = ldv_vec(psi, vg);
+          x = ld_vec<COOP>(psi, vg);
         }
         Acc pv;
         if constexpr (V == 1) {
@@ -320,9 +369,203 @@ __device__ void combine_observe(Shared<Real>& s, int n, int T, Vec* psi, const V
     }
   }
   block_reduce_write<kBatchMaxAtoms + 1>(out, s.red, s.tot, n + 1);
+  if (COOP) {
+    // the cluster's total, in rank order, broadcast by rank 0
+    if (threadIdx.x <= n) st_cluster(cluster_addr(&s.cpart[rank][threadIdx.x], 0), s.tot[threadIdx.x]);
+    cluster_sync();
+    if (rank == 0 && threadIdx.x <= n) {
+      double t = 0.0;
+      for (unsigned r = 0; r < ncl; ++r) t += s.cpart[r][threadIdx.x];
+      bcast(&s.tot[threadIdx.x], t, ncl);
+    }
+    cluster_sync();
+  }
 }
 
 }  // namespace
+
+// Evolves register `ri` over its whole pulse sequence. COOP: every CTA of the
+// cluster runs this with the same register; chunks are split by cluster rank,
+// partial sums meet in rank 0's shared memory, and rank 0 takes every Krylov
+// decision and broadcasts it, so all CTAs follow the same control flow and
+// meet at the same cluster barriers.
+template <typename Real, bool COOP>
+__device__ void process_register(const BatchArgs& A, Shared<Real>& s, Vec* s_x, Real* s_q, Vec* states, Vec* work,
+                                 int ri, unsigned rank, unsigned ncl) {
+  constexpr int TB = BatchCfg<Real>::TB;
+  constexpr int V = CplxT<Real>::kLogVec;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const BatchItem it = A.items[ri];
+  const int n = it.n;
+  const int T = n < TB ? n : TB;
+  const int64_t DV = (int64_t(1) << n) >> V;  // vectors per Krylov vector
+  Vec* psi = states + (it.state_off >> V);
+  Vec* u = work + (int64_t)A.m_max * DV;
+  const double* Vm = A.vmat + it.vmat_off;
+  for (int i = tid; i < n * n; i += kThreads) s.V[i / n][i % n] = Vm[i];
+  __syncthreads();
+  // Q[t] = sum_{q<r<T} V_qr t_q t_r over the low bits of b (FP64, rounded once)
+  for (int t = tid; t < (1 << T); t += kThreads) {
+    double e = 0.0;
+    for (int r = 1; r < T; ++r) {
+      if (!((t >> r) & 1)) continue;
+      for (int q = 0; q < r; ++q)
+        if ((t >> q) & 1) e += s.V[q][r];
+    }
+    s_q[t] = (Real)e;
+  }
+  // initial |psi|^2 and occupation row 0
+  combine_observe<Real, COOP>(s, n, T, psi, nullptr, 0, 0, false, rank, ncl);
+  double norm2 = s.tot[0];
+  int row = 0;
+  auto record = [&](int r) {
+    if (rank == 0 && r < it.occ_rows && tid < n) A.occ[it.occ_off + (int64_t)r * n + tid] = s.tot[1 + (n - 1 - tid)];
+  };
+  record(row++);
+  int last_m = 0;
+  int64_t iters = 0, subs = 0;
+  double max_err = 0.0;
+  int status = 0;
+  const int steps = A.step_limit > 0 && A.step_limit < it.steps ? A.step_limit : it.steps;
+  for (int step = 0; step < steps && status == 0; ++step) {
+    const double* P = A.params + it.param_off + (int64_t)step * (1 + 3 * n);
+    __syncthreads();
+    if (tid < n) {
+      // target bit 0: <0|h|1> = Omega/2 e^{+i phi}; target bit 1: <1|h|0> = Omega/2 e^{-i phi}
+      const double h = 0.5 * P[1 + tid];
+      const double ph = it.has_phi ? P[1 + 2 * n + tid] : 0.0;
+      const double cs = h * cos(ph), sn = h * sin(ph);
+      s.cp[tid][0] = make_coef<Real, true>((Real)cs, (Real)sn);
+      s.cp[tid][1] = make_coef<Real, true>((Real)cs, (Real)(-sn));
+      s.delta[tid] = P[1 + n + tid];
+    }
+    if (tid == 0) s.tau = P[0];
+    __syncthreads();
+    double tau_rem = s.tau;
+    int sub = 0;
+    while (tau_rem > 0.0 && norm2 > 0.0) {
+      const double b0 = sqrt(norm2);
+      const int check_from = last_m > 2 ? last_m - 2 : 1;
+      double a = 0.0, sc = 1.0 / b0, bprev = 0.0;
+      int m = 0;
+      for (int j = 0; j < A.m_max; ++j) {
+        Vec* bj = work + (int64_t)j * DV;
+        const Vec* bp = j > 0 ? work + (int64_t)(j - 1) * DV : nullptr;
+        const Vec* src = j == 0 ? psi : u;
+        if (it.has_phi)
+          lanczos_iteration<Real, true, COOP>(s, s_x, s_q, n, T, src, bj, bp, u, j, (Real)a, (Real)sc, (Real)bprev,
+                                              rank, ncl);
+        else
+          lanczos_iteration<Real, false, COOP>(s, s_x, s_q, n, T, src, bj, bp, u, j, (Real)a, (Real)sc,
+                                               (Real)bprev, rank, ncl);
+        ++iters;
+        m = j + 1;
+        if (COOP) {
+          // the CTAs' sums meet in rank 0
+          if (tid < 3) st_cluster(cluster_addr(&s.cpart[rank][tid], 0), s.tot[tid]);
+          cluster_sync();
+        }
+        if (warp == 0 && (!COOP || rank == 0)) {
+          double r3[3];
+#pragma unroll
+          for (int i = 0; i < 3; ++i) {
+            r3[i] = s.tot[i];
+            if (COOP) {
+              r3[i] = 0.0;
+              for (unsigned r = 0; r < ncl; ++r) r3[i] += s.cpart[r][i];
+            }
+          }
+          const LanczosScalars ls = lanczos_scalars(r3[0], r3[1], r3[2]);
+          const double alpha = ls.alpha, beta = ls.beta;
+          const int mk = ls.vanished ? m - 1 : m;  // accepted dimension if the space ends here
+          if (lane == 0) {
+            s.al[j] = alpha;
+            s.be[m] = beta;
+          }
+          __syncwarp();
+          double tn = 0.0;
+          for (int i = lane; i < mk; i += 32)
+            tn = fmax(tn, fabs(s.al[i]) + fabs(s.be[i + 1]) + (i > 0 ? fabs(s.be[i]) : 0.0));
+#pragma unroll
+          for (int off = 16; off > 0; off >>= 1) tn = fmax(tn, __shfl_xor_sync(0xffffffffu, tn, off));
+          const bool breakdown = ls.vanished || beta <= A.breakdown * fmax(tn, 1e-300);
+          const bool check = breakdown || m >= check_from || m >= A.m_max;
+          const KrylovDecision d = krylov_decide(s.al, s.be, mk, ls.vanished ? 0.0 : beta, tau_rem, breakdown,
+                                                 check, A.m_max, A.tol, s.ur, s.ui, s.cw);
+          if (d.status != kContinue) {
+            for (int i = lane; i < mk; i += 32) {
+              const Coef cf = make_coef<Real, true>((Real)(b0 * s.ur[i]), (Real)(b0 * s.ui[i]));
+              if (COOP) {
+                bcast(&s.cf[i].rr, cf.rr, ncl);
+                bcast(&s.cf[i].ii, cf.ii, ncl);
+              } else {
+                s.cf[i] = cf;
+              }
+            }
+          }
+          if (lane == 0) {
+            if (COOP) {
+              bcast(&s.m, mk, ncl);
+              bcast(&s.status, (int)d.status, ncl);
+              bcast(&s.tau_take, d.tau_take, ncl);
+              bcast(&s.err, d.err, ncl);
+              bcast(&s.alpha, alpha, ncl);
+              bcast(&s.beta, beta, ncl);
+            } else {
+              s.m = mk;
+              s.status = d.status;
+              s.tau_take = d.tau_take;
+              s.err = d.err;
+              s.alpha = alpha;
+              s.beta = beta;
+            }
+          }
+        }
+        if (COOP)
+          cluster_sync();  // the decision is in every CTA's shared memory
+        else
+          __syncthreads();
+        if (s.status != kContinue) {
+          m = s.m;
+          break;
+        }
+        a = s.alpha;
+        sc = 1.0 / s.beta;
+        bprev = s.beta;
+      }
+      const int st = s.status;
+      const double take = s.tau_take;
+      max_err = fmax(max_err, s.err);
+      last_m = m;
+      double rem = tau_rem - take;
+      if (st == kDone || rem <= 1e-14 * tau_rem) rem = 0.0;
+      combine_observe<Real, COOP>(s, n, T, psi, work, DV, m, true, rank, ncl);
+      norm2 = s.tot[0];
+      tau_rem = rem;
+      if (tau_rem > 0.0) {
+        ++sub;
+        ++subs;
+        if (sub > A.max_substeps) {
+          status = -3;
+          break;
+        }
+      }
+    }
+    const int done = step + 1;
+    if ((it.obs_stride > 0 && done % it.obs_stride == 0) || done == steps) record(row++);
+  }
+  if (tid == 0 && rank == 0) {
+    BatchOut o;
+    o.iterations = iters;
+    o.substeps = subs;
+    o.max_err = max_err;
+    o.norm2 = norm2;
+    o.status = status;
+    o.rows = row < it.occ_rows ? row : it.occ_rows;
+    A.out[ri] = o;
+  }
+  __syncthreads();
+}
 
 template <typename Real>
 __global__ void __launch_bounds__(kThreads, 2) batch_kernel(const BatchArgs A) {
@@ -332,176 +575,97 @@ __global__ void __launch_bounds__(kThreads, 2) batch_kernel(const BatchArgs A) {
   Vec* s_x = reinterpret_cast<Vec*>(dyn);
   Real* s_q = reinterpret_cast<Real*>(dyn + (2 * sizeof(Real) << TB));
   __shared__ Shared<Real> s;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tid = threadIdx.x;
   Vec* states = reinterpret_cast<Vec*>(A.states);
-  Vec* work = reinterpret_cast<Vec*>(A.work) + (int64_t)blockIdx.x * (A.work_stride >> V);
+  const int64_t wstride = A.work_stride >> V;
+  Vec* work = reinterpret_cast<Vec*>(A.work) + (int64_t)blockIdx.x * wstride;
 
+  // Phase 1: the large registers, one whole cluster each (the workspace of the
+  // cluster's rank-0 CTA holds the shared Krylov vectors).
+  const unsigned ncl = (unsigned)A.cluster;
+  if (ncl > 1 && A.count_large > 0) {
+    const unsigned rank = cluster_rank();
+    Vec* cwork = reinterpret_cast<Vec*>(A.work) + (int64_t)(blockIdx.x - rank) * wstride;
+    for (;;) {
+      if (rank == 0 && tid == 0) bcast(&s.item, atomicAdd(&A.next[0], 1), ncl);
+      cluster_sync();
+      const int qi = s.item;
+      cluster_sync();  // every CTA read s.item before the next broadcast
+      if (qi >= A.count_large) break;
+      process_register<Real, true>(A, s, s_x, s_q, states, cwork, A.order[qi], rank, ncl);
+    }
+  }
+  // Phase 2: the other registers, one CTA each.
   for (;;) {
-    if (tid == 0) s.item = atomicAdd(A.next, 1);
+    if (tid == 0) s.item = A.count_large + atomicAdd(&A.next[1], 1);
     __syncthreads();
     const int qi = s.item;
+    __syncthreads();
     if (qi >= A.count) break;
-    const BatchItem it = A.items[A.order[qi]];
-    const int n = it.n;
-    const int T = n < TB ? n : TB;
-    const int64_t DV = (int64_t(1) << n) >> V;  // vectors per Krylov vector
-    Vec* psi = states + (it.state_off >> V);
-    Vec* u = work + (int64_t)A.m_max * DV;
-    const double* Vm = A.vmat + it.vmat_off;
-    for (int i = tid; i < n * n; i += kThreads) s.V[i / n][i % n] = Vm[i];
-    __syncthreads();
-    // Q[t] = sum_{q<r<T} V_qr t_q t_r over the low bits of b (FP64, rounded once)
-    for (int t = tid; t < (1 << T); t += kThreads) {
-      double e = 0.0;
-      for (int r = 1; r < T; ++r) {
-        if (!((t >> r) & 1)) continue;
-        for (int q = 0; q < r; ++q)
-          if ((t >> q) & 1) e += s.V[q][r];
-      }
-      s_q[t] = (Real)e;
-    }
-    // initial |psi|^2 and occupation row 0
-    combine_observe<Real>(s, n, T, psi, nullptr, 0, 0, false);
-    double norm2 = s.tot[0];
-    int row = 0;
-    auto record = [&](int r) {
-      if (r < it.occ_rows && tid < n) A.occ[it.occ_off + (int64_t)r * n + tid] = s.tot[1 + (n - 1 - tid)];
-    };
-    record(row++);
-    int last_m = 0;
-    int64_t iters = 0, subs = 0;
-    double max_err = 0.0;
-    int status = 0;
-    const int steps = A.step_limit > 0 && A.step_limit < it.steps ? A.step_limit : it.steps;
-    for (int step = 0; step < steps && status == 0; ++step) {
-      const double* P = A.params + it.param_off + (int64_t)step * (1 + 3 * n);
-      __syncthreads();
-      if (tid < n) {
-        // target bit 0: <0|h|1> = Omega/2 e^{+i phi}; target bit 1: <1|h|0> = Omega/2 e^{-i phi}
-        const double h = 0.5 * P[1 + tid];
-        const double ph = it.has_phi ? P[1 + 2 * n + tid] : 0.0;
-        const double cs = h * cos(ph), sn = h * sin(ph);
-        s.cp[tid][0] = make_coef<Real, true>((Real)cs, (Real)sn);
-        s.cp[tid][1] = make_coef<Real, true>((Real)cs, (Real)(-sn));
-        s.delta[tid] = P[1 + n + tid];
-      }
-      if (tid == 0) s.tau = P[0];
-      __syncthreads();
-      double tau_rem = s.tau;
-      int sub = 0;
-      while (tau_rem > 0.0 && norm2 > 0.0) {
-        const double b0 = sqrt(norm2);
-        const int check_from = last_m > 2 ? last_m - 2 : 1;
-        double a = 0.0, sc = 1.0 / b0, bprev = 0.0;
-        int m = 0;
-        for (int j = 0; j < A.m_max; ++j) {
-          Vec* bj = work + (int64_t)j * DV;
-          const Vec* bp = j > 0 ? work + (int64_t)(j - 1) * DV : nullptr;
-          const Vec* src = j == 0 ? psi : u;
-          if (it.has_phi)
-            lanczos_iteration<Real, true>(s, s_x, s_q, n, T, src, bj, bp, u, j, (Real)a, (Real)sc, (Real)bprev);
-          else
-            lanczos_iteration<Real, false>(s, s_x, s_q, n, T, src, bj, bp, u, j, (Real)a, (Real)sc, (Real)bprev);
-          ++iters;
-          m = j + 1;
-          if (warp == 0) {
-            const LanczosScalars ls = lanczos_scalars(s.tot[0], s.tot[1], s.tot[2]);
-            const double alpha = ls.alpha, beta = ls.beta;
-            const int mk = ls.vanished ? m - 1 : m;  // accepted dimension if the space ends here
-            if (lane == 0) {
-              s.al[j] = alpha;
-              s.be[m] = beta;
-            }
-            __syncwarp();
-            double tn = 0.0;
-            for (int i = lane; i < mk; i += 32)
-              tn = fmax(tn, fabs(s.al[i]) + fabs(s.be[i + 1]) + (i > 0 ? fabs(s.be[i]) : 0.0));
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) tn = fmax(tn, __shfl_xor_sync(0xffffffffu, tn, off));
-            const bool breakdown = ls.vanished || beta <= A.breakdown * fmax(tn, 1e-300);
-            const bool check = breakdown || m >= check_from || m >= A.m_max;
-            const KrylovDecision d = krylov_decide(s.al, s.be, mk, ls.vanished ? 0.0 : beta, tau_rem, breakdown,
-                                                   check, A.m_max, A.tol, s.ur, s.ui, s.cw);
-            if (d.status != kContinue) {
-              for (int i = lane; i < mk; i += 32)
-                s.cf[i] = make_coef<Real, true>((Real)(b0 * s.ur[i]), (Real)(b0 * s.ui[i]));
-            }
-            if (lane == 0) {
-              s.m = mk;
-              s.status = d.status;
-              s.tau_take = d.tau_take;
-              s.err = d.err;
-              s.alpha = alpha;
-              s.beta = beta;
-            }
-          }
-          __syncthreads();
-          if (s.status != kContinue) {
-            m = s.m;
-            break;
-          }
-          a = s.alpha;
-          sc = 1.0 / s.beta;
-          bprev = s.beta;
-        }
-        const int st = s.status;
-        const double take = s.tau_take;
-        max_err = fmax(max_err, s.err);
-        last_m = m;
-        double rem = tau_rem - take;
-        if (st == kDone || rem <= 1e-14 * tau_rem) rem = 0.0;
-        combine_observe<Real>(s, n, T, psi, work, DV, m, true);
-        norm2 = s.tot[0];
-        tau_rem = rem;
-        if (tau_rem > 0.0) {
-          ++sub;
-          ++subs;
-          if (sub > A.max_substeps) {
-            status = -3;
-            break;
-          }
-        }
-      }
-      const int done = step + 1;
-      if ((it.obs_stride > 0 && done % it.obs_stride == 0) || done == steps) record(row++);
-    }
-    if (tid == 0) {
-      BatchOut o;
-      o.iterations = iters;
-      o.substeps = subs;
-      o.max_err = max_err;
-      o.norm2 = norm2;
-      o.status = status;
-      o.rows = row < it.occ_rows ? row : it.occ_rows;
-      A.out[A.order[qi]] = o;
-    }
-    __syncthreads();
+    process_register<Real, false>(A, s, s_x, s_q, states, work, A.order[qi], 0, 1);
   }
 }
 
-cudaError_t launch_batch(const BatchArgs& a, bool c64, int grid, cudaStream_t stream) {
-  if (c64)
-    batch_kernel<float><<<grid, kThreads, batch_dynamic_smem<float>(), stream>>>(a);
-  else
-    batch_kernel<double><<<grid, kThreads, batch_dynamic_smem<double>(), stream>>>(a);
-  return cudaGetLastError();
+namespace {
+
+template <typename Real>
+cudaError_t launch_typed(const BatchArgs& a, int grid, cudaStream_t stream) {
+  if (a.cluster <= 1) {
+    batch_kernel<Real><<<grid, kThreads, batch_dynamic_smem<Real>(), stream>>>(a);
+    return cudaGetLastError();
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid, 1, 1);
+  cfg.blockDim = dim3(kThreads, 1, 1);
+  cfg.dynamicSmemBytes = batch_dynamic_smem<Real>();
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = a.cluster;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, batch_kernel<Real>, a);
 }
 
-int batch_prepare(bool c64) {
-  int nb = 0;
+template <typename Real>
+int prepare_typed(int cluster, int* max_clusters) {
   // several CTAs per SM need the shared-memory side of the L1/shared split
-  if (c64) {
-    cudaFuncSetAttribute(batch_kernel<float>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    cudaFuncSetAttribute(batch_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)batch_dynamic_smem<float>());
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_kernel<float>, kThreads, batch_dynamic_smem<float>());
-  } else {
-    cudaFuncSetAttribute(batch_kernel<double>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    cudaFuncSetAttribute(batch_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)batch_dynamic_smem<double>());
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_kernel<double>, kThreads, batch_dynamic_smem<double>());
+  cudaFuncSetAttribute(batch_kernel<Real>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  cudaFuncSetAttribute(batch_kernel<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)batch_dynamic_smem<Real>());
+  int nb = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_kernel<Real>, kThreads, batch_dynamic_smem<Real>());
+  *max_clusters = 0;
+  if (cluster > 1) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cluster, 1, 1);
+    cfg.blockDim = dim3(kThreads, 1, 1);
+    cfg.dynamicSmemBytes = batch_dynamic_smem<Real>();
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (cudaOccupancyMaxActiveClusters(max_clusters, batch_kernel<Real>, &cfg) != cudaSuccess) {
+      cudaGetLastError();
+      *max_clusters = 0;
+    }
   }
   return nb;
+}
+
+}  // namespace
+
+cudaError_t launch_batch(const BatchArgs& a, bool c64, int grid, cudaStream_t stream) {
+  return c64 ? launch_typed<float>(a, grid, stream) : launch_typed<double>(a, grid, stream);
+}
+
+int batch_prepare(bool c64, int cluster, int* max_clusters) {
+  return c64 ? prepare_typed<float>(cluster, max_clusters) : prepare_typed<double>(cluster, max_clusters);
 }
 
 }  // namespace rsv

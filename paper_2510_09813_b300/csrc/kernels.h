@@ -105,6 +105,8 @@ cudaError_t launch_combine(const CombineArgs& a, bool c64, int grid, cudaStream_
 
 // Batched evolution of many small registers (batch_kernels.cu).
 constexpr int kBatchMaxAtoms = 20;
+constexpr int kBatchCluster = 4;    // CTAs of a thread-block cluster sharing one large register
+constexpr int kBatchCoopAtoms = 15; // registers of at least this many atoms go to a whole cluster
 
 struct BatchItem {       // one register, device descriptor
   int32_t n;             // atoms
@@ -132,7 +134,9 @@ struct BatchArgs {
   const BatchItem* items;
   const int* order;      // processing order (largest registers first)
   int count;
-  int* next;             // work counter, 0 at launch
+  int count_large;       // order[0 .. count_large) are solved by whole clusters
+  int cluster;           // CTAs per cluster of the launch (1: no cooperative phase)
+  int* next;             // work counters [large, small], 0 at launch
   void* states;
   const double* params;
   const double* vmat;
@@ -147,9 +151,10 @@ struct BatchArgs {
   double breakdown;
 };
 cudaError_t launch_batch(const BatchArgs& a, bool c64, int grid, cudaStream_t stream);
-// Sets the kernel's shared-memory attribute (call before launching or capturing)
-// and returns the resident CTAs per SM.
-int batch_prepare(bool c64);
+// Sets the kernel's shared-memory attributes (call before launching or
+// capturing); returns the resident CTAs per SM and, for cluster > 1, the
+// clusters of that size that can be resident at once (0: none).
+int batch_prepare(bool c64, int cluster, int* max_clusters);
 
 // Sampling (sample_kernels.cu)
 cudaError_t launch_block_sums(const void* psi, int64_t dim, bool c64, int64_t chunk, double* sums, cudaStream_t stream);

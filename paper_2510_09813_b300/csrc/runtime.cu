@@ -1477,6 +1477,8 @@ struct rsv_batch {
   int nmax = 0;
   int grid = 0;
   int blocks_per_sm = 0;
+  int count_large = 0;  // registers solved by whole clusters (the front of `order`)
+  int cluster = 1;      // CTAs per cluster of the launch
   int64_t work_stride = 0;
   size_t state_amps = 0;
   std::vector<BatchItem> items;
@@ -1522,6 +1524,8 @@ struct rsv_batch {
     a.items = d_items;
     a.order = d_order;
     a.count = count;
+    a.count_large = count_large;
+    a.cluster = cluster;
     a.next = d_next;
     a.states = d_states;
     a.params = d_params;
@@ -1554,6 +1558,10 @@ rsv_status batch_tune_krylov(rsv_batch* b) {
   const int ns = std::min(b->count, 48);
   std::vector<int> sample(ns);
   for (int i = 0; i < ns; ++i) sample[i] = b->order[(size_t)i * b->count / ns];
+  int ns_large = 0;  // the sample keeps the order: cooperative registers first
+  for (int i = 0; i < ns; ++i) ns_large += i * b->count / ns < b->count_large ? 1 : 0;
+  const int sample_grid =
+      std::min(b->grid, (ns + b->cluster - 1) / b->cluster * b->cluster);  // a multiple of the cluster size
   int* d_sample = nullptr;
   RSV_TRY(b->alloc(sizeof(int) * ns, (void**)&d_sample));
   RSV_CUDA(cudaMemcpyAsync(d_sample, sample.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, b->stream));
@@ -1564,12 +1572,13 @@ rsv_status batch_tune_krylov(rsv_batch* b) {
     BatchArgs a = b->args();
     a.order = d_sample;
     a.count = ns;
+    a.count_large = ns_large;
     a.m_max = cand[c < 0 ? 0 : c];  // c = -1: warm-up launch
     a.step_limit = kBatchTuneSteps;
     RSV_CUDA(cudaMemcpyAsync(b->d_states, b->d_init, sbytes, cudaMemcpyDeviceToDevice, b->stream));
-    RSV_CUDA(cudaMemsetAsync(b->d_next, 0, sizeof(int), b->stream));
+    RSV_CUDA(cudaMemsetAsync(b->d_next, 0, sizeof(int) * 2, b->stream));
     RSV_CUDA(cudaEventRecord(b->ev0, b->stream));
-    RSV_CUDA(launch_batch(a, b->c64, std::min(ns, b->grid), b->stream));
+    RSV_CUDA(launch_batch(a, b->c64, sample_grid, b->stream));
     RSV_CUDA(cudaEventRecord(b->ev1, b->stream));
     RSV_CUDA(cudaStreamSynchronize(b->stream));
     float ms = 0.f;
@@ -1605,7 +1614,7 @@ rsv_status batch_capture(rsv_batch* b) {
   const size_t sbytes = b->state_amps * amp_bytes(b->cfg.precision);
   RSV_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
   cudaError_t e = cudaMemcpyAsync(b->d_states, b->d_init, sbytes, cudaMemcpyDeviceToDevice, b->stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(b->d_next, 0, sizeof(int), b->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->d_next, 0, sizeof(int) * 2, b->stream);
   if (e == cudaSuccess) e = launch_batch(b->args(), b->c64, b->grid, b->stream);
   cudaGraph_t g = nullptr;
   const cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
@@ -1698,15 +1707,28 @@ rsv_status rsv_batch_create(rsv_ctx* ctx, const rsv_problem* problems, int32_t c
   // largest registers first
   b->order.resize(count);
   for (int r = 0; r < count; ++r) b->order[r] = r;
+  // registers of kBatchCoopAtoms or more atoms first (each solved by a whole
+  // cluster), then the rest; largest work first within each group
+  auto large = [&](int x) { return b->items[x].n >= kBatchCoopAtoms; };
   std::stable_sort(b->order.begin(), b->order.end(), [&](int x, int y) {
+    if (large(x) != large(y)) return large(x);
     const int64_t wx = (int64_t)b->items[x].steps << b->items[x].n, wy = (int64_t)b->items[y].steps << b->items[y].n;
     return wx > wy;
   });
+  for (int r = 0; r < count; ++r) b->count_large += large(r) ? 1 : 0;
   std::lock_guard<std::mutex> lk(ctx->mu);
   cudaSetDevice(ctx->device);
-  b->blocks_per_sm = batch_prepare(b->c64);
+  int max_clusters = 0;
+  b->blocks_per_sm = batch_prepare(b->c64, b->count_large > 0 ? kBatchCluster : 1, &max_clusters);
   if (b->blocks_per_sm < 1) return fail(RSV_ERR_CUDA, "batched kernel does not fit on an SM");
-  b->grid = std::min(count, b->blocks_per_sm * ctx->num_sms);
+  if (b->count_large > 0 && max_clusters > 0) {
+    b->cluster = kBatchCluster;
+    const int want = (count + kBatchCluster - 1) / kBatchCluster;
+    b->grid = std::min(want, max_clusters) * kBatchCluster;
+  } else {
+    b->count_large = 0;  // no cluster launch possible: every register on one CTA
+    b->grid = std::min(count, b->blocks_per_sm * ctx->num_sms);
+  }
   b->work_stride = (int64_t)(cfg.m_max + 1) << b->nmax;
   rsv_status st = RSV_OK;
   auto A = [&](size_t bytes, void** p) {
@@ -1714,7 +1736,7 @@ rsv_status rsv_batch_create(rsv_ctx* ctx, const rsv_problem* problems, int32_t c
   };
   A(sizeof(BatchItem) * count, (void**)&b->d_items);
   A(sizeof(int) * count, (void**)&b->d_order);
-  A(sizeof(int), (void**)&b->d_next);
+  A(sizeof(int) * 2, (void**)&b->d_next);
   A(b->state_amps * ab, &b->d_states);
   A(b->state_amps * ab, &b->d_init);
   A(sizeof(double) * params.size(), (void**)&b->d_params);

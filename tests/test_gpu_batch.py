@@ -110,6 +110,21 @@ def test_batch_matches_solver_up_to_18_atoms(ctx):
     b.close()
 
 
+@pytest.mark.parametrize("prec,sizes", [("c128", [15, 16, 11]), ("c64", [17, 15, 12, 9])])
+def test_batch_cooperative_registers_match_oracle(ctx, prec, sizes):
+    """Registers of 15 atoms and more are solved by a whole thread-block cluster
+    (chunks split across its CTAs, sums and Krylov decisions through
+    distributed shared memory); smaller ones in the same launch by one CTA."""
+    probs = mixed_problems(16, sizes, 50, with_phi=True)
+    b = api().Batch(ctx, probs, 10, prec, obs_stride=1)
+    b.run()
+    for i, p in enumerate(probs):
+        ref, occ_ref = oracle_evolve(p, 10)
+        assert O.infidelity(b.state(i).astype(np.complex128), ref) <= INFID_TOL[prec]
+        assert np.max(np.abs(b.occupations(i) - occ_ref)) <= OCC_TOL[prec]
+    b.close()
+
+
 def test_batch_rerun_is_identical_and_restarts(ctx):
     """A second run (graph replay) repeats the first bit for bit; a small m_max
     forces substeps that must not change the result beyond tolerance."""
