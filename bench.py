@@ -190,7 +190,7 @@ def reference_arm(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
-    n_sample = 22
+    n_sample = 20  # about 3 s per sample: K + W samples end within a few minutes
     for _ in range(args.warmup):
         oracle_step_sample(n_sample)
     walls, cores = [], 1

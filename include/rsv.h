@@ -336,7 +336,9 @@ RSV_API void rsv_batch_destroy(rsv_batch* b);
 
 typedef struct {
   int32_t slots;        /* solves in flight at once, each on its own CUDA stream; default 4 */
-  int32_t reserved;     /* must be 0 */
+  int32_t batch_atoms;  /* 0: off. Else a request of at most this many atoms (<= 20) is solved together
+                           with the queued requests of the same size and config that fit (up to 64) by
+                           one batched launch (rsv_batch_*); pays off for bursts of like requests */
   size_t memory_bytes;  /* device bytes admitted solves may hold together. 0: the context arena's
                            free bytes at creation (capped context), else 90% of the device's free
                            memory */
@@ -350,8 +352,9 @@ typedef struct {
  * basis, work vectors, tables: the bytes its solver allocates) fits next to
  * the solves already running, so requests arriving while others run are
  * admitted as slots and memory free up, and their work overlaps on the device.
- * A capped context arena is recommended: its allocations need no device-wide
- * synchronisation. */
+ * Each request runs the streaming solver on its own stream, or joins a
+ * batched launch (config->batch_atoms). A capped context arena is
+ * recommended: its allocations need no device-wide synchronisation. */
 RSV_API rsv_status rsv_server_create(rsv_ctx* ctx, const rsv_server_config* config, rsv_server** out);
 /* Queues one solve (the problem and config are copied; the call does not
  * wait). RSV_ERR_OUT_OF_MEMORY if its footprint exceeds the server's memory. */

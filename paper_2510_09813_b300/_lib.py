@@ -54,7 +54,7 @@ KERNEL_KINDS = ("pass_first", "pass_second", "control", "combine")
 
 
 class ServerConfig_(C.Structure):
-    _fields_ = [("slots", C.c_int32), ("reserved", C.c_int32), ("memory_bytes", C.c_size_t),
+    _fields_ = [("slots", C.c_int32), ("batch_atoms", C.c_int32), ("memory_bytes", C.c_size_t),
                 ("max_bypass_s", C.c_double)]
 
 

@@ -387,10 +387,12 @@ class Server:
     """rsv_server: solves submitted at any time, admitted by device footprint,
     run concurrently on their own streams (continuous batching)."""
 
-    def __init__(self, ctx: Context, slots: int = 4, memory_bytes: int = 0, max_bypass_s: float = 0.0):
+    def __init__(self, ctx: Context, slots: int = 4, memory_bytes: int = 0, max_bypass_s: float = 0.0,
+                 batch_atoms: int = 0):
         self.ctx = ctx
         cfg = L.ServerConfig_()
-        cfg.slots, cfg.reserved, cfg.memory_bytes, cfg.max_bypass_s = int(slots), 0, int(memory_bytes), float(max_bypass_s)
+        cfg.slots, cfg.batch_atoms = int(slots), int(batch_atoms)
+        cfg.memory_bytes, cfg.max_bypass_s = int(memory_bytes), float(max_bypass_s)
         self._h = C.c_void_p()
         check(L.lib().rsv_server_create(ctx.handle, C.byref(cfg), C.byref(self._h)))
         self._precision = {}

@@ -695,7 +695,11 @@ struct rsv_solver {
 // Result
 // ---------------------------------------------------------------------------
 struct rsv_result {
-  rsv_solver* solver = nullptr;
+  rsv_ctx* ctx = nullptr;
+  int n = 0, precision = 0;
+  rsv_solver* solver = nullptr;           // a streaming solve, owned by the result
+  std::shared_ptr<rsv_batch> batch;       // or a register of a batched solve (shared by its results)
+  int index = 0;
   std::vector<double> occ;
   int rows = 0;
   double wait_s = 0.0;     // served requests: submission to admission
@@ -1383,6 +1387,9 @@ rsv_status rsv_solver_stats(const rsv_solver* s, rsv_stats* out) {
 static rsv_status make_result(rsv_solver* s, rsv_result** out) {
   rsv_ctx* ctx = s->ctx;
   auto r = new rsv_result();
+  r->ctx = ctx;
+  r->n = s->n;
+  r->precision = s->precision;
   r->solver = s;
   r->service_s = s->stats.seconds;
   {
@@ -1418,11 +1425,13 @@ rsv_status rsv_run(rsv_ctx* ctx, const rsv_problem* problem, const rsv_config* c
 
 rsv_status rsv_result_state(const rsv_result* r, void* host_dst, size_t bytes) {
   if (!r) return fail(RSV_ERR_INVALID_ARG, "NULL result");
+  if (r->batch) return rsv_batch_state(r->batch.get(), r->index, host_dst, bytes);
   return rsv_solver_get_state(r->solver, host_dst, bytes);
 }
 
 rsv_status rsv_result_state_device(const rsv_result* r, void** dev_ptr, size_t* bytes) {
   if (!r) return fail(RSV_ERR_INVALID_ARG, "NULL result");
+  if (r->batch) return rsv_batch_state_device(r->batch.get(), r->index, dev_ptr, bytes);
   return rsv_solver_state_device(r->solver, dev_ptr, bytes);
 }
 
@@ -1431,18 +1440,22 @@ rsv_status rsv_result_occupations(const rsv_result* r, double* dst, int32_t capa
   *n_rows = r->rows;
   if (dst) {
     const int rows = std::min(capacity_rows, r->rows);
-    std::memcpy(dst, r->occ.data(), sizeof(double) * rows * r->solver->n);
+    std::memcpy(dst, r->occ.data(), sizeof(double) * rows * r->n);
   }
   return RSV_OK;
 }
 
 rsv_status rsv_result_sample(const rsv_result* r, int64_t shots, uint64_t seed, uint64_t* out) {
   if (!r) return fail(RSV_ERR_INVALID_ARG, "NULL result");
-  return rsv_sample(r->solver->ctx, r->solver->n, r->solver->precision, r->solver->d_psi, shots, seed, out);
+  void* psi = nullptr;
+  size_t bytes = 0;
+  RSV_TRY(rsv_result_state_device(r, &psi, &bytes));
+  return rsv_sample(r->ctx, r->n, r->precision, psi, shots, seed, out);
 }
 
 rsv_status rsv_result_stats(const rsv_result* r, rsv_stats* out) {
   if (!r) return fail(RSV_ERR_INVALID_ARG, "NULL result");
+  if (r->batch) return rsv_batch_stats(r->batch.get(), r->index, out);
   return rsv_solver_stats(r->solver, out);
 }
 
@@ -1456,11 +1469,11 @@ rsv_status rsv_result_times(const rsv_result* r, double* wait_s, double* service
 void rsv_result_free(rsv_result* r) {
   if (!r) return;
   {
-    std::lock_guard<std::mutex> lk(r->solver->ctx->mu);
-    r->solver->ctx->results.erase(r);
+    std::lock_guard<std::mutex> lk(r->ctx->mu);
+    r->ctx->results.erase(r);
   }
   delete r->solver;  // owned by the result, not in the context's solver set
-  delete r;
+  delete r;          // a batch goes with its last result
 }
 
 }  // extern "C"
@@ -1764,15 +1777,17 @@ rsv_status rsv_batch_create(rsv_ctx* ctx, const rsv_problem* problems, int32_t c
   return RSV_OK;
 }
 
-rsv_status rsv_batch_run(rsv_batch* b) {
-  g_last_error.clear();
-  if (!b) return fail(RSV_ERR_INVALID_ARG, "NULL batch");
-  std::lock_guard<std::mutex> lk(b->ctx->mu);
+}  // extern "C"
+
+// Replays the batch's graph and waits for it. `after_ctx`: first order it
+// after the context stream's earlier work (the caller's inputs).
+static rsv_status batch_run(rsv_batch* b, bool after_ctx) {
   cudaSetDevice(b->ctx->device);
   b->have_out = false;
-  // ordered after the context stream's earlier work (inputs written there)
-  RSV_CUDA(cudaEventRecord(b->ev_in, b->ctx->stream));
-  RSV_CUDA(cudaStreamWaitEvent(b->stream, b->ev_in, 0));
+  if (after_ctx) {
+    RSV_CUDA(cudaEventRecord(b->ev_in, b->ctx->stream));
+    RSV_CUDA(cudaStreamWaitEvent(b->stream, b->ev_in, 0));
+  }
   RSV_CUDA(cudaEventRecord(b->ev0, b->stream));
   RSV_CUDA(cudaGraphLaunch(b->exec, b->stream));
   RSV_CUDA(cudaEventRecord(b->ev1, b->stream));
@@ -1787,6 +1802,15 @@ rsv_status rsv_batch_run(rsv_batch* b) {
       return fail(RSV_ERR_NOT_CONVERGED, "register " + std::to_string(r) + ": Krylov step needed more than " +
                                              std::to_string(b->cfg.max_substeps) + " substeps");
   return RSV_OK;
+}
+
+extern "C" {
+
+rsv_status rsv_batch_run(rsv_batch* b) {
+  g_last_error.clear();
+  if (!b) return fail(RSV_ERR_INVALID_ARG, "NULL batch");
+  std::lock_guard<std::mutex> lk(b->ctx->mu);
+  return batch_run(b, true);
 }
 
 rsv_status rsv_batch_state_device(const rsv_batch* b, int32_t index, void** dev_ptr, size_t* bytes) {
@@ -1883,9 +1907,12 @@ struct ServeRequest {
 
 }  // namespace
 
+constexpr int kServeBatchMax = 64;  // requests per batched launch
+
 struct rsv_server {
   rsv_ctx* ctx = nullptr;
   int slots = 0;
+  int batch_atoms = 0;  // 0: every request on the streaming solver
   size_t budget = 0, in_use = 0;
   double max_bypass_s = 0.5;
   std::mutex mu;
@@ -1913,6 +1940,46 @@ struct rsv_server {
     return queue.end();
   }
 
+  // Requests of up to batch_atoms atoms with the same size and config are taken
+  // from the queue together and solved by one batched-kernel launch (every step
+  // on the device, no host round trip per iteration).
+  bool batchable(const ServeRequest* r) const { return r->prob.n_atoms <= batch_atoms; }
+  static bool same_class(const ServeRequest* a, const ServeRequest* b) {
+    return a->prob.n_atoms == b->prob.n_atoms && std::memcmp(&a->cfg, &b->cfg, sizeof(rsv_config)) == 0;
+  }
+
+  rsv_status serve_group(const std::vector<ServeRequest*>& g, std::vector<rsv_result*>& out) {
+    std::vector<rsv_problem> probs;
+    for (const ServeRequest* q : g) probs.push_back(q->prob);
+    rsv_batch* b = nullptr;
+    rsv_status st = rsv_batch_create(ctx, probs.data(), (int32_t)g.size(), &g[0]->cfg, &b);
+    if (st == RSV_OK) st = batch_run(b, false);
+    if (st != RSV_OK) {
+      if (b) rsv_batch_destroy(b);
+      return st;
+    }
+    std::shared_ptr<rsv_batch> holder(b, [](rsv_batch* p) { rsv_batch_destroy(p); });
+    for (size_t i = 0; i < g.size(); ++i) {
+      auto res = new rsv_result();
+      res->ctx = ctx;
+      res->n = g[i]->prob.n_atoms;
+      res->precision = g[i]->cfg.precision;
+      res->batch = holder;
+      res->index = (int)i;
+      int32_t rows = 0;
+      rsv_batch_occupations(b, (int32_t)i, nullptr, 0, &rows);
+      res->occ.resize((size_t)rows * res->n);
+      rsv_batch_occupations(b, (int32_t)i, res->occ.data(), rows, &rows);
+      res->rows = rows;
+      {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        ctx->results.insert(res);
+      }
+      out[i] = res;
+    }
+    return RSV_OK;
+  }
+
   rsv_status serve(ServeRequest* r, rsv_result** out) {
     cudaStream_t st = nullptr;
     RSV_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
@@ -1934,36 +2001,55 @@ struct rsv_server {
   void worker() {
     cudaSetDevice(ctx->device);
     for (;;) {
-      ServeRequest* r = nullptr;
+      std::vector<ServeRequest*> g;
       {
         std::unique_lock<std::mutex> lk(mu);
         // a bypass window closing changes pick(): re-check at least every 50 ms
         while (!stop && pick() == queue.end()) cv_work.wait_for(lk, std::chrono::milliseconds(50));
         if (stop) return;
         auto it = pick();
-        r = *it;
+        g.push_back(*it);
         queue.erase(it);
-        in_use += r->bytes;
-        ++running;
-        r->state = 1;
-        r->t_admit = now();
+        in_use += g[0]->bytes;
+        if (batchable(g[0])) {
+          for (auto jt = queue.begin(); jt != queue.end() && (int)g.size() < kServeBatchMax;) {
+            ServeRequest* q = *jt;
+            if (same_class(q, g[0]) && q->bytes <= budget - in_use) {
+              in_use += q->bytes;
+              g.push_back(q);
+              jt = queue.erase(jt);
+            } else {
+              ++jt;
+            }
+          }
+        }
+        const double t = now();
+        for (ServeRequest* q : g) {
+          q->state = 1;
+          q->t_admit = t;
+        }
+        running += (int)g.size();
       }
-      rsv_result* res = nullptr;
-      const rsv_status st = serve(r, &res);
+      std::vector<rsv_result*> res(g.size(), nullptr);
+      const rsv_status st = batchable(g[0]) ? serve_group(g, res) : serve(g[0], &res[0]);
       const std::string err = st == RSV_OK ? std::string() : g_last_error;
       {
         std::lock_guard<std::mutex> lk(mu);
-        r->t_done = now();
-        r->status = st;
-        r->error = err;
-        r->result = res;
-        if (res) {
-          res->wait_s = r->t_admit - r->t_submit;
-          res->service_s = r->t_done - r->t_admit;
+        const double t = now();
+        for (size_t i = 0; i < g.size(); ++i) {
+          ServeRequest* q = g[i];
+          q->t_done = t;
+          q->status = st;
+          q->error = err;
+          q->result = res[i];
+          if (res[i]) {
+            res[i]->wait_s = q->t_admit - q->t_submit;
+            res[i]->service_s = q->t_done - q->t_admit;
+          }
+          q->state = 2;
+          in_use -= q->bytes;
+          --running;
         }
-        r->state = 2;
-        in_use -= r->bytes;
-        --running;
       }
       cv_done.notify_all();
       cv_work.notify_all();
@@ -1979,12 +2065,14 @@ rsv_status rsv_server_create(rsv_ctx* ctx, const rsv_server_config* config, rsv_
   *out = nullptr;
   rsv_server_config cfg{};
   if (config) cfg = *config;
-  if (cfg.reserved != 0) return fail(RSV_ERR_INVALID_ARG, "reserved must be 0");
+  if (cfg.batch_atoms < 0 || cfg.batch_atoms > kBatchMaxAtoms)
+    return fail(RSV_ERR_INVALID_ARG, "batch_atoms must be in [0, " + std::to_string(kBatchMaxAtoms) + "]");
   if (cfg.slots == 0) cfg.slots = 4;
   if (cfg.slots < 1 || cfg.slots > 64) return fail(RSV_ERR_INVALID_ARG, "slots must be in [1, 64]");
   std::unique_ptr<rsv_server> srv(new rsv_server());
   srv->ctx = ctx;
   srv->slots = cfg.slots;
+  srv->batch_atoms = cfg.batch_atoms;
   srv->max_bypass_s = cfg.max_bypass_s == 0.0 ? 0.5 : cfg.max_bypass_s;
   {
     std::lock_guard<std::mutex> lk(ctx->mu);

@@ -47,24 +47,52 @@ def requests(seed, sizes, t_lo=60, t_hi=200):
 
 
 def test_results_alone_equal_in_mix(ctx):
-    reqs = requests(21, [14, 9, 20, 12, 17, 11, 22, 15, 8, 19, 13, 16])
+    """Each request's result is the same served alone and served in a mix of
+    requests that run concurrently on their own streams."""
+    reqs = requests(21, [14, 9, 20, 12, 17, 11, 22, 15, 8, 19, 13, 16, 12, 12, 9, 9])
     srv = api().Server(ctx, slots=4)
     tickets = [srv.submit(p, 10, prec, obs_stride=1) for p, prec in reqs]
     results = [srv.poll(t, timeout_ms=-1) for t in tickets]
     srv.close()
-    identical = 0
     for (p, prec), r in zip(reqs, results):
-        alone = api().run(ctx, p, 10, prec, obs_stride=1)
-        a, b = alone.state().astype(np.complex128), r.state().astype(np.complex128)
-        assert O.infidelity(b, a) <= INFID_TOL[prec]
-        assert np.max(np.abs(r.occupations() - alone.occupations())) <= OCC_TOL[prec]
-        identical += int(np.array_equal(a, b))
-        w, s = r.times()
-        assert w >= 0.0 and s > 0.0
-        alone.close()
-        r.close()
-    # same kernels, same reductions: the mix changes nothing at all
-    assert identical == len(reqs)
+        one = api().Server(ctx, slots=1)
+        alone = one.poll(one.submit(p, 10, prec, obs_stride=1))
+        a, b = alone.state(), r.state()
+        # same kernels, same fixed reduction trees: the mix changes nothing at all
+        assert np.array_equal(a, b)
+        assert np.array_equal(alone.occupations(), r.occupations())
+        # and against the streaming solver run directly, within the tolerance
+        ref = api().run(ctx, p, 10, prec, obs_stride=1)
+        assert O.infidelity(b.astype(np.complex128), ref.state().astype(np.complex128)) <= INFID_TOL[prec]
+        assert np.max(np.abs(r.occupations() - ref.occupations())) <= OCC_TOL[prec]
+        w, sv = r.times()
+        assert w >= 0.0 and sv > 0.0
+        for x in (alone, ref, r):
+            x.close()
+        one.close()
+
+
+def test_batched_lane_groups_like_requests(ctx):
+    """With batch_atoms set, like requests queued together are solved by one
+    batched launch (they share admission and completion times) and give the
+    same results as each request served alone."""
+    probs = [W.random_knot_problem(np.random.Generator(np.random.PCG64([31, k])), 10, 100) for k in range(8)]
+    srv = api().Server(ctx, slots=1, batch_atoms=14)
+    tickets = [srv.submit(p, 10, "c64", obs_stride=1) for p in probs]
+    results = [srv.poll(t) for t in tickets]
+    srv.close()
+    service = [r.times()[1] for r in results]
+    # the first request may have started alone before the others were queued
+    assert max(service.count(v) for v in service) >= 2
+    for p, r in zip(probs, results):
+        one = api().Server(ctx, slots=1, batch_atoms=14)
+        alone = one.poll(one.submit(p, 10, "c64", obs_stride=1))
+        assert np.array_equal(alone.state(), r.state())
+        ref = api().run(ctx, p, 10, "c64", obs_stride=1)
+        assert O.infidelity(r.state().astype(np.complex128), ref.state().astype(np.complex128)) <= INFID_TOL["c64"]
+        for x in (alone, ref, r):
+            x.close()
+        one.close()
 
 
 def test_served_result_matches_oracle(ctx):
