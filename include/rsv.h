@@ -144,10 +144,12 @@ RSV_API const char* rsv_last_error(void);
 /* Library version string. */
 RSV_API const char* rsv_version(void);
 
-/* Device bytes a solve of n_atoms at `precision` with Krylov cap m_max holds:
- * the state, m_max basis vectors, two work vectors and the tables. This is the
- * admission footprint; Sec. III.A.1 gives the same accounting for the paper's
- * complex128 emulator (16 * 2^N bytes per vector). */
+/* Device bytes a solve of n_atoms at `precision` with Krylov cap m_max holds
+ * apart from its sequence: the state, m_max basis vectors, two work vectors,
+ * the per-tile diagonal rows and 2 MiB of tables and partial sums. A solver
+ * adds its per-step parameters and recorded occupation rows (the admission
+ * checks count those too). Sec. III.A.1 gives the same accounting for the
+ * paper's complex128 emulator (16 * 2^N bytes per vector). */
 RSV_API size_t rsv_footprint_bytes(int32_t n_atoms, int32_t precision, int32_t m_max);
 
 /* ---- host-side preparation (Sec. II.A, Sec. III) ---------------------------- */
