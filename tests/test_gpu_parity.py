@@ -8,6 +8,7 @@ Tolerances (complex128 path / complex64 path):
   * occupations: max |d<n_i>| <= 1e-10 / 1e-5.
 """
 import math
+import os
 
 import numpy as np
 import pytest
@@ -143,9 +144,11 @@ def test_rabi_chain_n8(ctx, rabi_chain_ref, prec):
 
 @pytest.fixture(scope="module")
 def sweep_3x4_ref():
+    # the oracle's full 400-step evolution, written by tests/golden/make_sweep_3x4.py
+    # (about ten minutes of CPU); test_oracle_pins checks its first steps afresh
     prob = W.adiabatic_sweep_lattice(3, 4)
-    psi, occ = oracle_evolve(prob, 10)
-    return prob, psi, occ
+    with np.load(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "sweep_3x4_dt10.npz")) as g:
+        return prob, g["psi"], g["occ"]
 
 
 @pytest.mark.parametrize("prec", ["c128", "c64"])
@@ -305,6 +308,33 @@ def test_n28_norm_conservation_random_box(ctx):
     n2, occ = api().observe(ctx, 28, "c64", torch.from_numpy(s.state()).cuda())
     assert abs(n2 - 1.0) <= 1e-5
     assert np.all(occ >= -1e-7) and np.all(occ <= 1 + 1e-6)
+
+
+def test_n28_full_sequence_conserves_norm_and_energy(ctx):
+    """The whole 2 us random box (400 steps of a constant Hamiltonian, complex64,
+    m_max 20): |psi| stays 1 and <H> stays at its initial value 0 (|0...0> has
+    E = 0 and no drive expectation). Every step's Krylov error is at most
+    tol = 1e-7 relative, so |Delta <H>| <= 2 * 400 * tol * |H|; FP32 rounding of
+    the 2^28-term inner product adds ~1e-6 |H|. The bound used, 1e-4 |H|, is
+    above both."""
+    prob = W.random_box(seed=3, n=28)
+    s = api().Solver(ctx, prob, 5, "c64", m_max=20, obs_stride=0)
+    s.run_to_end()
+    assert s.progress() == (400, 400)
+    psi = torch.from_numpy(s.state()).cuda()
+    s.close()
+    V = O.pair_interactions(prob.positions, prob.c6)
+    om, de = prob.omega[:, 0], prob.delta[:, 0]
+    h = api().Hamiltonian(ctx, 28, "c64", V, om, de, None)
+    y = torch.empty_like(psi)
+    h.apply(psi, y)
+    h.sync()
+    h.close()
+    n2 = float(torch.sum(torch.abs(psi.to(torch.complex128)) ** 2))
+    energy = complex(torch.vdot(psi.to(torch.complex128), y.to(torch.complex128)))
+    assert abs(n2 - 1.0) <= 1e-5
+    assert abs(energy.imag) <= 1e-4 * scale_of(V, om, de)
+    assert abs(energy.real) <= 1e-4 * scale_of(V, om, de)
 
 
 # ---------------------------------------------------------------------------

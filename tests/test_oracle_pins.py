@@ -389,3 +389,19 @@ def test_hamiltonian_rows_match_dense():
     x = rng.standard_normal(2 ** n) + 1j * rng.standard_normal(2 ** n)
     idx = [0, 1, 17, 40, 63]
     assert np.allclose(O.hamiltonian_rows(idx, x, V, om, de, ph), (H @ x)[idx], atol=1e-10)
+
+
+def test_sweep_3x4_golden_matches_the_oracle():
+    """The stored 400-step evolution of the 3x4 sweep (GPU parity reference) is
+    the oracle's: its first 12 occupation rows are recomputed here, and its
+    final state is normalised."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "sweep_3x4_dt10.npz")
+    with np.load(path) as g:
+        psi, occ = g["psi"], g["occ"]
+    assert psi.shape == (2 ** 12,) and occ.shape == (401, 12)
+    assert abs(np.linalg.norm(psi) - 1.0) < 1e-12
+    prob = W.adiabatic_sweep_lattice(3, 4)
+    t_ns = 110
+    _, occ_head = O.evolve(prob.positions, prob.c6, t_ns, 10, prob.omega[:, :t_ns], prob.delta[:, :t_ns], None,
+                           method="krylov", tol=1e-14)
+    assert np.max(np.abs(np.asarray(occ_head) - occ[:12])) <= 1e-12
