@@ -196,12 +196,25 @@ RSV_API rsv_status rsv_hamiltonian_apply(rsv_hamiltonian* h, const void* x_dev, 
  * bounded wait gave up. */
 RSV_API rsv_status rsv_hamiltonian_sync(rsv_hamiltonian* h);
 RSV_API void rsv_hamiltonian_destroy(rsv_hamiltonian* h);
+/* Energy moments of a device state psi (2^n amplitudes, the operator's
+ * precision, unnormalised): out[0] + i out[1] = <psi|H|psi>, out[2] =
+ * <psi|H^2|psi> = |H psi|^2, accumulated to FP64-class accuracy (host array of
+ * 3). Uses one vector of context-arena scratch; synchronises the context
+ * stream. */
+RSV_API rsv_status rsv_hamiltonian_expectation(rsv_hamiltonian* h, const void* psi_dev, double* out);
 
 /* |psi|^2 and <n_i> = sum_b |psi_b|^2 b_i (atom order) of a device state,
  * accumulated to FP64; results copied to the host arrays (occ may be NULL).
  * Synchronises the context stream. */
 RSV_API rsv_status rsv_observe(rsv_ctx* ctx, int32_t n_atoms, int32_t precision, const void* psi_dev, double* norm2_out,
                        double* occ_out);
+
+/* Pair correlations C[i][j] = sum_b |psi_b|^2 b_i b_j (atom order; C[i][i] =
+ * <n_i> unnormalised) of a device state, accumulated to FP64, written to the
+ * host array out[n_atoms][n_atoms]. One observation pass per atom: the pass
+ * for atom i counts only amplitudes with b_i = 1. Synchronises the context
+ * stream. */
+RSV_API rsv_status rsv_correlations(rsv_ctx* ctx, int32_t n_atoms, int32_t precision, const void* psi_dev, double* out);
 
 /* `shots` basis indices drawn from |psi_b|^2 / |psi|^2 of a device state by
  * inverse CDF (FP64 running sums). Shot s uses Philox4x32-10 with counter

@@ -321,6 +321,25 @@ def occupations(psi: np.ndarray) -> np.ndarray:
     return out
 
 
+def correlations(psi: np.ndarray) -> np.ndarray:
+    """<n_i n_j> = sum_b |psi_b|^2 b_i b_j for every pair of atoms (diagonal:
+    <n_i>), as the bit matrix product B^T diag(p) B over basis indices b."""
+    n = int(round(math.log2(psi.size)))
+    p = psi.real.astype(np.float64) ** 2 + psi.imag.astype(np.float64) ** 2
+    b = np.arange(psi.size)
+    B = np.stack([(b >> (n - 1 - i)) & 1 for i in range(n)], axis=1).astype(np.float64)
+    return B.T @ (p[:, None] * B)
+
+
+def energy_moments(psi: np.ndarray, V, omega_bar, delta_bar, phi_bar=None):
+    """(<psi|H|psi>, <psi|H^2|psi>) for the Hamiltonian of Eq. (3) with the
+    given (constant) parameters; <H^2> = |H psi|^2 since H is Hermitian."""
+    psi = np.asarray(psi, dtype=np.complex128)
+    phi = np.zeros(V.shape[0]) if phi_bar is None else phi_bar
+    y = apply_hamiltonian(psi, V, omega_bar, delta_bar, phi)
+    return complex(np.vdot(psi, y)), float(np.vdot(y, y).real)
+
+
 def evolve(positions, c6, t_ns, dt_ns, omega, delta, phi=None, psi0=None,
            method: str = "krylov", tol: float = 1e-13, m_max: int = 60,
            record_occupations: bool = True):

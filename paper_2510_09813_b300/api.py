@@ -144,6 +144,12 @@ class Hamiltonian:
     def sync(self):
         check(L.lib().rsv_hamiltonian_sync(self._h))
 
+    def expectation(self, psi) -> tuple[complex, float]:
+        """(<psi|H|psi>, <psi|H^2|psi>) of a CUDA state tensor (unnormalised)."""
+        out = np.empty(3)
+        check(L.lib().rsv_hamiltonian_expectation(self._h, _check_state(psi, self.n, self.precision), L._dptr(out)))
+        return complex(out[0], out[1]), float(out[2])
+
     def close(self):
         if self._h:
             L.lib().rsv_hamiltonian_destroy(self._h)
@@ -163,6 +169,14 @@ def observe(ctx: Context, n_atoms: int, precision, psi):
     check(L.lib().rsv_observe(ctx.handle, int(n_atoms), precision_code(precision),
                               _check_state(psi, n_atoms, precision), C.byref(norm2), L._dptr(occ)))
     return norm2.value, occ
+
+
+def correlations(ctx: Context, n_atoms: int, precision, psi) -> np.ndarray:
+    """C[i][j] = sum_b |psi_b|^2 b_i b_j (atom order) of a CUDA state tensor."""
+    out = np.empty((n_atoms, n_atoms))
+    check(L.lib().rsv_correlations(ctx.handle, int(n_atoms), precision_code(precision),
+                                   _check_state(psi, n_atoms, precision), L._dptr(out)))
+    return out
 
 
 def observe_static(n_atoms: int, precision, psi, out, stream=None):

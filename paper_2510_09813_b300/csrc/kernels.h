@@ -100,6 +100,7 @@ struct CombineArgs {
   void* psi;               // output (COMBINE) or input (observe only)
   double* partials;        // [grid][n+1]
   int combine;
+  int mask_bit = -1;       // observe only: >= 0 counts only amplitudes whose bit mask_bit is 1
 };
 cudaError_t launch_combine(const CombineArgs& a, bool c64, int grid, cudaStream_t stream);
 
@@ -155,6 +156,11 @@ cudaError_t launch_batch(const BatchArgs& a, bool c64, int grid, cudaStream_t st
 // capturing); returns the resident CTAs per SM and, for cluster > 1, the
 // clusters of that size that can be resident at once (0: none).
 int batch_prepare(bool c64, int cluster, int* max_clusters);
+
+// Inner products for expectation values (observable_kernels.cu): per block
+// Re<x, y>, Im<x, y>, |y|^2 (FP64-class), partials[grid][3].
+cudaError_t launch_dot3(const void* x, const void* y, int64_t dim, bool c64, double* partials, int grid,
+                        cudaStream_t stream);
 
 // Sampling (sample_kernels.cu)
 cudaError_t launch_block_sums(const void* psi, int64_t dim, bool c64, int64_t chunk, double* sums, cudaStream_t stream);

@@ -234,6 +234,17 @@ __global__ void __launch_bounds__(kThreads) combine_kernel(const CombineArgs A) 
         reinterpret_cast<vec*>(A.psi)[vidx] = *reinterpret_cast<const vec*>(x);
       } else {
         *reinterpret_cast<vec*>(x) = reinterpret_cast<const vec*>(A.psi)[vidx];
+        if (A.mask_bit >= 0) {
+          // restrict to amplitudes whose bit mask_bit is 1
+#pragma unroll
+          for (int e = 0; e < NV; ++e) {
+            const int64_t b = (vidx << V) | e;
+            if (!((b >> A.mask_bit) & 1)) {
+              x[2 * e] = 0;
+              x[2 * e + 1] = 0;
+            }
+          }
+        }
       }
       Acc pv;  // this vector's total
 #pragma unroll

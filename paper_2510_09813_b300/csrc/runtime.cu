@@ -1088,6 +1088,82 @@ rsv_status rsv_observe(rsv_ctx* ctx, int32_t n_atoms, int32_t precision, const v
   return RSV_OK;
 }
 
+rsv_status rsv_correlations(rsv_ctx* ctx, int32_t n_atoms, int32_t precision, const void* psi_dev, double* out) {
+  g_last_error.clear();
+  if (!ctx || !psi_dev || !out) return fail(RSV_ERR_INVALID_ARG, "NULL argument");
+  if (n_atoms < 1 || n_atoms > 31) return fail(RSV_ERR_INVALID_ARG, "n_atoms out of range");
+  if (precision != RSV_C64 && precision != RSV_C128) return fail(RSV_ERR_INVALID_ARG, "bad precision");
+  if (reinterpret_cast<uintptr_t>(psi_dev) & 15) return fail(RSV_ERR_INVALID_ARG, "psi must be 16-byte aligned");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  cudaSetDevice(ctx->device);
+  const bool c64 = precision == RSV_C64;
+  const Plan plan = make_plan(n_atoms, c64, ctx->num_sms);
+  std::vector<double> rows((size_t)n_atoms * n_atoms);
+  for (int i = 0; i < n_atoms; ++i) {
+    // row i: the occupations of psi restricted to amplitudes with atom i excited
+    CombineArgs ca{};
+    ca.n = n_atoms;
+    ca.dim = int64_t(1) << n_atoms;
+    ca.ks = ctx->d_ks;
+    ca.psi = const_cast<void*>(psi_dev);
+    ca.partials = ctx->d_part;
+    ca.combine = 0;
+    ca.mask_bit = n_atoms - 1 - i;
+    RSV_CUDA(launch_combine(ca, c64, plan.grid_c, ctx->stream));
+    BeginArgs ba{};
+    ba.ks = ctx->d_ks;
+    ba.partials = ctx->d_part;
+    ba.nparts = plan.grid_c;
+    ba.n = n_atoms;
+    ba.occ_out = ctx->d_occ;
+    ba.reset_only = 1;
+    RSV_CUDA(launch_begin(ba, ctx->stream));
+    RSV_CUDA(cudaMemcpyAsync(rows.data() + (size_t)i * n_atoms, ctx->d_occ, sizeof(double) * n_atoms,
+                             cudaMemcpyDeviceToHost, ctx->stream));
+  }
+  RSV_CUDA(cudaStreamSynchronize(ctx->stream));
+  std::memcpy(out, rows.data(), rows.size() * sizeof(double));
+  return RSV_OK;
+}
+
+rsv_status rsv_hamiltonian_expectation(rsv_hamiltonian* h, const void* psi_dev, double* out) {
+  g_last_error.clear();
+  if (!h || !psi_dev || !out) return fail(RSV_ERR_INVALID_ARG, "NULL argument");
+  if (reinterpret_cast<uintptr_t>(psi_dev) & 15) return fail(RSV_ERR_INVALID_ARG, "psi must be 16-byte aligned");
+  rsv_ctx* ctx = h->ctx;
+  const int64_t dim = int64_t(1) << h->n;
+  const size_t vbytes = (size_t)dim * amp_bytes(h->c64 ? RSV_C64 : RSV_C128);
+  void* y = nullptr;
+  RSV_TRY(ctx->arena.alloc(vbytes, &y));
+  struct Release {
+    rsv_ctx* c;
+    void* p;
+    ~Release() {
+      cudaStreamSynchronize(c->stream);
+      c->arena.release(p);
+    }
+  } release{ctx, y};
+  RSV_TRY(rsv_hamiltonian_apply(h, psi_dev, y));
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  cudaSetDevice(ctx->device);
+  const int grid = 4 * ctx->num_sms;
+  RSV_CUDA(launch_dot3(psi_dev, y, dim, h->c64, ctx->d_part, grid, ctx->stream));
+  std::vector<double> part((size_t)grid * 3);
+  int err = 0;
+  RSV_CUDA(cudaMemcpyAsync(part.data(), ctx->d_part, part.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                           ctx->stream));
+  RSV_CUDA(cudaMemcpyAsync(&err, err_ptr(h->d_ks), sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  RSV_CUDA(cudaStreamSynchronize(ctx->stream));
+  if (err) return fail(RSV_ERR_TIMEOUT, "a device-side wait timed out (kernel aborted)");
+  double s[3] = {0.0, 0.0, 0.0};
+  for (int b = 0; b < grid; ++b)
+    for (int k = 0; k < 3; ++k) s[k] += part[(size_t)b * 3 + k];
+  out[0] = s[0];
+  out[1] = s[1];
+  out[2] = s[2];
+  return RSV_OK;
+}
+
 rsv_status rsv_sample(rsv_ctx* ctx, int32_t n_atoms, int32_t precision, const void* psi_dev, int64_t shots,
                       uint64_t seed, uint64_t* out) {
   g_last_error.clear();

@@ -405,3 +405,34 @@ def test_sweep_3x4_golden_matches_the_oracle():
     _, occ_head = O.evolve(prob.positions, prob.c6, t_ns, 10, prob.omega[:, :t_ns], prob.delta[:, :t_ns], None,
                            method="krylov", tol=1e-14)
     assert np.max(np.abs(np.asarray(occ_head) - occ[:12])) <= 1e-12
+
+
+def test_correlations_and_energy_moments():
+    """Product states: <n_i n_j> = <n_i><n_j> for i != j and <n_i n_i> = <n_i>.
+    A basis state at Omega = 0 is an eigenstate: <H> = E(b), variance 0. A
+    single atom from |0> with Omega, delta: <H> = 0 and <H^2> = Omega^2 / 4."""
+    rng = np.random.Generator(np.random.PCG64(41))
+    n = 6
+    ab = W.random_product_state(5, n)
+    psi = ab[0]
+    for i in range(1, n):
+        psi = np.kron(psi, ab[i])
+    C = O.correlations(psi)
+    occ = O.occupations(psi)
+    assert np.allclose(np.diag(C), occ, atol=1e-14)
+    off = C - np.outer(occ, occ)
+    np.fill_diagonal(off, 0.0)
+    assert np.max(np.abs(off)) < 1e-14
+    # basis state b at Omega = 0
+    pos = W.random_register(rng, n, 20.0)
+    V = O.pair_interactions(pos, W.C6_DEFAULT)
+    de = rng.normal(0, 3, n)
+    b = 0b101101
+    e = np.zeros(2 ** n, dtype=np.complex128)
+    e[b] = 1.0
+    E1, E2 = O.energy_moments(e, V, np.zeros(n), de)
+    Eb = O.diagonal_energies(V, de)[b]
+    assert abs(E1 - Eb) < 1e-9 * max(1.0, abs(Eb)) and abs(E2 - Eb ** 2) < 1e-9 * max(1.0, Eb ** 2)
+    # one atom from |0>: H|0> = Omega/2 |1>
+    E1, E2 = O.energy_moments(np.array([1.0, 0.0]), np.zeros((1, 1)), np.array([3.0]), np.array([1.5]))
+    assert abs(E1) < 1e-15 and abs(E2 - 9.0 / 4.0) < 1e-14
