@@ -347,6 +347,21 @@ RSV_API rsv_status rsv_batch_occupations(const rsv_batch* b, int32_t index, doub
 RSV_API rsv_status rsv_batch_stats(const rsv_batch* b, int32_t index, rsv_stats* out);
 RSV_API void rsv_batch_destroy(rsv_batch* b);
 
+/* ---- shot-to-shot noise: averages over perturbed copies of one problem --------- */
+
+/* Evolves `shots` copies of `problem`, copy s with Omega scaled by
+ * omega_scale[s], delta shifted by delta_shift[s] (rad/us) and, if
+ * pos_shift_um is not NULL, atom i displaced by pos_shift_um[(s * n_atoms + i)
+ * * dim + k] (um), and writes the mean of their occupation rows to occ_mean
+ * [rows][n_atoms] (host; the rows of rsv_solver_occupations). Sec. III.A names
+ * shot-to-shot variation of the Hamiltonian parameters as one way the emulator
+ * models noise; the random draws are the caller's inputs. Copies of at most 20
+ * atoms run as one batched launch (rsv_batch_*), larger ones one by one. NULL
+ * occ_mean queries *n_rows. */
+RSV_API rsv_status rsv_run_shots(rsv_ctx* ctx, const rsv_problem* problem, const rsv_config* config, int32_t shots,
+                                 const double* omega_scale, const double* delta_shift, const double* pos_shift_um,
+                                 double* occ_mean, int32_t capacity_rows, int32_t* n_rows);
+
 /* ---- serving: continuous admission of solves by device-memory footprint ------- */
 
 typedef struct {

@@ -91,6 +91,8 @@ def lib():
             "rsv_hamiltonian_destroy": (None, [P]),
             "rsv_hamiltonian_expectation": (I32, [P, P, PD]),
             "rsv_correlations": (I32, [P, I32, I32, P, PD]),
+            "rsv_run_shots": (I32, [P, C.POINTER(Problem_), C.POINTER(Config_), I32, PD, PD, PD, PD, I32,
+                                    C.POINTER(I32)]),
             "rsv_sample": (I32, [P, I32, I32, P, I64, U64, C.POINTER(C.c_uint64)]),
             "rsv_observe_static": (I32, [I32, I32, P, P, P]),
             "rsv_solver_create": (I32, [P, C.POINTER(Problem_), C.POINTER(Config_), C.POINTER(P)]),

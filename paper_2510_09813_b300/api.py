@@ -451,6 +451,31 @@ class Server:
             pass
 
 
+def run_shots(ctx: Context, problem, dt_ns: int, omega_scale, delta_shift, pos_shift_um=None, precision="c64",
+              krylov_tol=0.0, m_max=0, max_substeps=0, obs_stride=1) -> np.ndarray:
+    """rsv_run_shots: mean occupation rows over perturbed copies of `problem`
+    (copy s: Omega * omega_scale[s], delta + delta_shift[s], positions +
+    pos_shift_um[s]); the draws are the caller's."""
+    pa = L.ProblemArgs.from_problem(problem)
+    cfg = L.make_config(dt_ns, precision, krylov_tol, m_max, max_substeps, obs_stride)
+    sc = np.ascontiguousarray(np.asarray(omega_scale, dtype=np.float64))
+    sh = np.ascontiguousarray(np.asarray(delta_shift, dtype=np.float64))
+    if sc.shape != sh.shape or sc.ndim != 1:
+        raise ValueError("omega_scale and delta_shift must be 1-D of the same length")
+    ps = None
+    if pos_shift_um is not None:
+        ps = np.ascontiguousarray(np.asarray(pos_shift_um, dtype=np.float64))
+        if ps.shape != (sc.size,) + pa.pos.shape:
+            raise ValueError("pos_shift_um must be [shots][n_atoms][dim]")
+    rows = C.c_int32()
+    args = (ctx.handle, C.byref(pa.struct), C.byref(cfg), int(sc.size), L._dptr(sc), L._dptr(sh),
+            L._dptr(ps) if ps is not None else C.POINTER(C.c_double)())
+    check(L.lib().rsv_run_shots(*args, C.POINTER(C.c_double)(), 0, C.byref(rows)))
+    out = np.empty((rows.value, pa.n))
+    check(L.lib().rsv_run_shots(*args, L._dptr(out), rows.value, C.byref(rows)))
+    return out
+
+
 def run(ctx: Context, problem, dt_ns: int, precision="c128", krylov_tol=0.0, m_max=0, max_substeps=0,
         obs_stride=1, initial_state=None) -> Result:
     """rsv_run: the whole sequence, host inputs in, a Result out."""

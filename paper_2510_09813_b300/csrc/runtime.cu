@@ -1961,6 +1961,77 @@ void rsv_batch_destroy(rsv_batch* b) {
 }  // extern "C"
 
 // ---------------------------------------------------------------------------
+// Shot-to-shot noise: perturbed copies of one problem, occupations averaged.
+// ---------------------------------------------------------------------------
+extern "C" rsv_status rsv_run_shots(rsv_ctx* ctx, const rsv_problem* problem, const rsv_config* config,
+                                    int32_t shots, const double* omega_scale, const double* delta_shift,
+                                    const double* pos_shift_um, double* occ_mean, int32_t capacity_rows,
+                                    int32_t* n_rows) {
+  g_last_error.clear();
+  if (!ctx || !config || !n_rows || !omega_scale || !delta_shift) return fail(RSV_ERR_INVALID_ARG, "NULL argument");
+  RSV_TRY(validate_problem(problem));
+  if (shots < 1) return fail(RSV_ERR_INVALID_ARG, "shots must be >= 1");
+  if (config->dt_ns < 1) return fail(RSV_ERR_INVALID_ARG, "dt_ns must be >= 1");
+  if (config->obs_stride < 0) return fail(RSV_ERR_INVALID_ARG, "obs_stride must be >= 0");
+  const int n = problem->n_atoms, T = problem->t_ns, dim = problem->dim;
+  const int steps = num_steps(T, config->dt_ns);
+  const int stride = config->obs_stride;
+  // rows recorded: t = 0, every stride-th step, and the end if not on a stride
+  const int rows = 1 + (stride > 0 ? steps / stride : 0) + ((stride == 0 || steps % stride != 0) ? 1 : 0);
+  if (!occ_mean) {
+    *n_rows = rows;
+    return RSV_OK;
+  }
+  // the perturbed copies (owned here for the duration of the call)
+  std::vector<std::vector<double>> pos(shots), om(shots), de(shots);
+  std::vector<rsv_problem> probs(shots);
+  for (int k = 0; k < shots; ++k) {
+    pos[k].assign(problem->positions_um, problem->positions_um + (size_t)n * dim);
+    if (pos_shift_um)
+      for (int i = 0; i < n * dim; ++i) pos[k][i] += pos_shift_um[(size_t)k * n * dim + i];
+    om[k].assign(problem->omega, problem->omega + (size_t)problem->omega_rows * T);
+    for (double& v : om[k]) v *= omega_scale[k];
+    de[k].assign(problem->delta, problem->delta + (size_t)problem->delta_rows * T);
+    for (double& v : de[k]) v += delta_shift[k];
+    probs[k] = *problem;
+    probs[k].positions_um = pos[k].data();
+    probs[k].omega = om[k].data();
+    probs[k].delta = de[k].data();
+  }
+  std::vector<double> sum((size_t)rows * n, 0.0);
+  std::vector<double> buf((size_t)rows * n);
+  int got_rows = rows;
+  if (n <= kBatchMaxAtoms) {
+    rsv_batch* b = nullptr;
+    RSV_TRY(rsv_batch_create(ctx, probs.data(), shots, config, &b));
+    rsv_status st = rsv_batch_run(b);
+    for (int k = 0; k < shots && st == RSV_OK; ++k) {
+      int32_t r = 0;
+      st = rsv_batch_occupations(b, k, buf.data(), rows, &r);
+      got_rows = std::min(got_rows, r);
+      for (size_t i = 0; i < (size_t)r * n; ++i) sum[i] += buf[i];
+    }
+    rsv_batch_destroy(b);
+    RSV_TRY(st);
+  } else {
+    for (int k = 0; k < shots; ++k) {
+      rsv_result* r = nullptr;
+      RSV_TRY(rsv_run(ctx, &probs[k], config, &r));
+      int32_t nr = 0;
+      const rsv_status st = rsv_result_occupations(r, buf.data(), rows, &nr);
+      rsv_result_free(r);
+      RSV_TRY(st);
+      got_rows = std::min(got_rows, nr);
+      for (size_t i = 0; i < (size_t)nr * n; ++i) sum[i] += buf[i];
+    }
+  }
+  *n_rows = got_rows;
+  const int r = std::min(capacity_rows, got_rows);
+  for (size_t i = 0; i < (size_t)r * n; ++i) occ_mean[i] = sum[i] / shots;
+  return RSV_OK;
+}
+
+// ---------------------------------------------------------------------------
 // Serving: requests are admitted by device-memory footprint; each admitted
 // solve runs on a worker thread with its own CUDA stream, so solves of
 // different requests overlap on the device.
