@@ -99,3 +99,16 @@ def test_create_without_gpu_fails_cleanly():
     h = C.c_void_p()
     st = L.lib().rsv_create(C.byref(h), 0, 0, None)
     assert st in (-5, -1) and not h.value
+
+
+def test_new_entries_reject_bad_arguments_without_a_gpu():
+    """Argument checks of the later entries run before any device work."""
+    lib = L.lib()
+    assert lib.rsv_correlations(None, 4, L.RSV_C64, None, None) == -1
+    assert lib.rsv_hamiltonian_expectation(None, None, None) == -1
+    assert lib.rsv_run_shots(None, None, None, 1, None, None, None, None, 0, None) == -1
+    assert lib.rsv_batch_run(None) == -1
+    assert lib.rsv_poll(None, 1, 0, None) == -1
+    assert lib.rsv_observe_static(4, L.RSV_C64, None, None, None) == -1
+    assert lib.rsv_observe_static(32, L.RSV_C64, C.c_void_p(16), C.c_void_p(16), None) == -1
+    assert b"limit of 31 atoms" in lib.rsv_last_error()
