@@ -162,15 +162,21 @@ def test_adiabatic_sweep_3x4_full_length(ctx, sweep_3x4_ref, prec):
     assert np.max(np.abs(occ - occ_ref)) <= OCC_TOL[prec]
 
 
-@pytest.mark.parametrize("prec", ["c128", "c64"])
-def test_adiabatic_sweep_4x5_window(ctx, prec):
-    """The 20-atom 4x5 lattice, three steps from t = 2 us of the sweep (peak drive,
-    delta crossing zero), from a random state: full-size geometry of both passes."""
+@pytest.fixture(scope="module")
+def sweep_4x5_window_ref():
     full = W.adiabatic_sweep_lattice(4, 5)
     lo, hi = 2000, 2020
     prob = W.Problem(full.positions, full.c6, hi - lo, full.omega[:, lo:hi], full.delta[:, lo:hi], None)
     psi0 = W.random_state(20, 20)
     ref, occ_ref = oracle_evolve(prob, 10, psi0=psi0)
+    return prob, psi0, ref, occ_ref
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+def test_adiabatic_sweep_4x5_window(ctx, sweep_4x5_window_ref, prec):
+    """The 20-atom 4x5 lattice, two steps from t = 2 us of the sweep (peak drive,
+    delta crossing zero), from a random state: full-size geometry of both passes."""
+    prob, psi0, ref, occ_ref = sweep_4x5_window_ref
     psi, occ, _ = gpu_evolve(ctx, prob, 10, prec, initial_state=psi0)
     assert O.infidelity(psi, ref) <= INFID_TOL[prec]
     if prec == "c128":
