@@ -1639,7 +1639,7 @@ constexpr int kBatchTuneSteps = 10;  // steps of each sampled register per candi
 
 // Krylov-depth autotuner of a batch: evolves a sample of the registers (spread
 // over the largest-first order) over their first kBatchTuneSteps steps with
-// each candidate m_max and keeps the fastest. A larger m_max means fewer substeps but more FP64 exponentials per
+// each candidate m_max (see the choice rule below). A larger m_max means fewer substeps but more FP64 exponentials per
 // step and a larger workspace; the best value depends on the registers'
 // spectra and time steps. The workspace is then shrunk to the chosen depth.
 rsv_status batch_tune_krylov(rsv_batch* b) {
@@ -1655,9 +1655,9 @@ rsv_status batch_tune_krylov(rsv_batch* b) {
   RSV_TRY(b->alloc(sizeof(int) * ns, (void**)&d_sample));
   RSV_CUDA(cudaMemcpyAsync(d_sample, sample.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, b->stream));
   const size_t sbytes = b->state_amps * amp_bytes(b->cfg.precision);
-  int best = b->cfg.m_max;
-  float best_ms = 1e30f;
-  for (int c = -1; c < (int)(sizeof(cand) / sizeof(cand[0])); ++c) {
+  const int ncand = (int)(sizeof(cand) / sizeof(cand[0]));
+  std::vector<float> cand_ms(ncand, 1e30f);
+  for (int c = -1; c < ncand; ++c) {
     BatchArgs a = b->args();
     a.order = d_sample;
     a.count = ns;
@@ -1676,11 +1676,16 @@ rsv_status batch_tune_krylov(rsv_batch* b) {
     RSV_CUDA(cudaMemcpy(o.data(), b->d_out, sizeof(BatchOut) * b->count, cudaMemcpyDeviceToHost));
     bool ok = true;
     for (int i : sample) ok = ok && o[i].status == 0;
-    if (c >= 0 && ok && ms < best_ms) {
-      best_ms = ms;
-      best = a.m_max;
-    }
+    if (c >= 0 && ok) cand_ms[c] = ms;
   }
+  // The sample covers only the first steps, while later steps of a sequence
+  // (a more entangled state) need larger Krylov spaces: take the largest depth
+  // within 10% of the fastest sample time.
+  float best_ms = 1e30f;
+  for (int c = 0; c < ncand; ++c) best_ms = std::min(best_ms, cand_ms[c]);
+  int best = b->cfg.m_max;
+  for (int c = 0; c < ncand; ++c)
+    if (cand_ms[c] <= 1.10f * best_ms) best = cand[c];
   b->cfg.m_max = best;
   b->tuned_ms = best_ms;
   // shrink the workspace to the chosen depth
