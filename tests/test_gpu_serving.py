@@ -2,7 +2,7 @@
 
 Requests of mixed size and precision are submitted while others run; each
 result must be the same as the same request solved alone (rsv_run on the
-same context) within the benchmark spec's tolerances (infidelity 1e-10 for
+same context) within the parity tolerances (infidelity 1e-10 for
 complex128, 1e-5 for complex64; occupations 1e-10 / 1e-5), and admission must
 keep the bytes held by running solves within the server's memory.
 """
