@@ -435,3 +435,109 @@ def sample_bitstrings(psi: np.ndarray, shots: int, seed: int) -> np.ndarray:
         idx = int(np.searchsorted(cdf, u * total, side="right"))
         out[s] = min(idx, psi.size - 1)
     return out
+
+
+# ---------------------------------------------------------------------------
+# Overlap with a target state (fidelity; Sec. III emulator results)
+# ---------------------------------------------------------------------------
+
+
+def overlap(a, b):
+    """(<a|b>, |a|^2, |b|^2) in complex128 / float64; the fidelity of b with
+    the target a is |<a|b>|^2 / (|a|^2 |b|^2)."""
+    a = np.asarray(a, dtype=np.complex128)
+    b = np.asarray(b, dtype=np.complex128)
+    return complex(np.vdot(a, b)), float(np.vdot(a, a).real), float(np.vdot(b, b).real)
+
+
+# ---------------------------------------------------------------------------
+# Gradients of an occupation observable with respect to the pulse samples.
+# Sec. V: the emulator is differentiable, i.e. derivatives of expectation
+# values with respect to the tensors that define the pulse sequence exist.
+# ---------------------------------------------------------------------------
+
+
+def drive_generators(n_atoms: int, i: int, omega_bar_i: float, phi_bar_i: float):
+    """dH/dOmega_i, dH/ddelta_i and dH/dphi_i of Eq. (3) (with the phase) as
+    dense matrices, entry by entry (brute force, small N).
+
+    Drive of atom i: <1|h|0> = Omega/2 e^{-i phi}, <0|h|1> = Omega/2 e^{+i phi}.
+    d/dOmega: 1/2 e^{-i phi} and 1/2 e^{+i phi}; d/dphi: -i Omega/2 e^{-i phi}
+    and +i Omega/2 e^{+i phi}; d/ddelta: -n_i on the diagonal."""
+    D = 2 ** n_atoms
+    g_om = np.zeros((D, D), dtype=np.complex128)
+    g_ph = np.zeros((D, D), dtype=np.complex128)
+    g_de = np.zeros((D, D), dtype=np.complex128)
+    bit = atom_bit(n_atoms, i)
+    for b in range(D):
+        bp = b ^ (1 << bit)
+        if (b >> bit) & 1 == 0:  # column b with b_i = 0, target row bp has b_i = 1
+            g_om[bp, b] = 0.5 * np.exp(-1j * phi_bar_i)
+            g_ph[bp, b] = -0.5j * omega_bar_i * np.exp(-1j * phi_bar_i)
+        else:
+            g_om[bp, b] = 0.5 * np.exp(1j * phi_bar_i)
+            g_ph[bp, b] = 0.5j * omega_bar_i * np.exp(1j * phi_bar_i)
+            g_de[b, b] = -1.0
+    return g_om, g_de, g_ph
+
+
+def midpoint_samples(t_ns: int, start_ns: int, length_ns: int):
+    """The two sample indices the midpoint rule averages (Sec. III), each with
+    weight 1/2 (they coincide when the midpoint falls on a sample)."""
+    twice_m = 2 * start_ns + length_ns
+    return min(twice_m // 2, t_ns - 1), min((twice_m + 1) // 2, t_ns - 1)
+
+
+def occupation_gradient(positions, c6, t_ns, dt_ns, omega, delta, phi=None, weights=None, psi0=None):
+    """Value and exact gradient of <O>(T) = <psi_K| sum_i w_i n_i |psi_K> with
+    respect to every pulse sample (brute force, N <= 8).
+
+    psi_{k+1} = U_k psi_k with U_k = exp(-i tau_k H_k) (Eq. (6)). For a step
+    parameter theta of H_k, d<O>/dtheta = 2 Re <lambda_{k+1}| dU_k/dtheta |psi_k>
+    with the costate lambda_K = O psi_K, lambda_k = U_k^dagger lambda_{k+1}.
+    dU_k/dtheta is the Frechet derivative of expm at -i tau_k H_k in the
+    direction -i tau_k dH/dtheta (scipy.linalg.expm_frechet, Al-Mohy and
+    Higham 2009), so no commutation of H_k with dH/dtheta is assumed. The
+    midpoint rule gives each step parameter the weight 1/2 on its two samples;
+    a pulse array with one row is shared by all atoms, so its gradient sums
+    over them.
+
+    Returns (value, d_omega, d_delta, d_phi) with the arrays shaped like the
+    inputs ([rows][t_ns]); d_phi is None when phi is None.
+    """
+    V = pair_interactions(positions, c6)
+    n = V.shape[0]
+    w = np.ones(n) if weights is None else np.asarray(weights, dtype=np.float64)
+    om = np.atleast_2d(np.asarray(omega, dtype=np.float64))
+    de = np.atleast_2d(np.asarray(delta, dtype=np.float64))
+    ph = None if phi is None else np.atleast_2d(np.asarray(phi, dtype=np.float64))
+    steps = step_parameters(n, t_ns, dt_ns, om, de, ph)
+    psi = zero_state(n) if psi0 is None else np.array(psi0, dtype=np.complex128)
+    Hs, Us, psis = [], [], [psi]
+    for tau, o, d, p in steps:
+        H = dense_hamiltonian(V, o, d, p)
+        U = scipy.linalg.expm(-1j * tau * H)
+        Hs.append(H)
+        Us.append(U)
+        psis.append(U @ psis[-1])
+    o_diag = occupation_bits(n) @ w
+    value = float(np.real(np.vdot(psis[-1], o_diag * psis[-1])))
+    d_om, d_de = np.zeros_like(om), np.zeros_like(de)
+    d_ph = None if ph is None else np.zeros_like(ph)
+    lam = o_diag * psis[-1]
+    schedule = step_schedule(t_ns, dt_ns)
+    for k in range(len(steps) - 1, -1, -1):
+        tau, o, d, p = steps[k]
+        lo, hi = midpoint_samples(t_ns, *schedule[k])
+        for i in range(n):
+            g_om, g_de, g_ph = drive_generators(n, i, o[i], p[i])
+            for G, target in ((g_om, d_om), (g_de, d_de), (g_ph, d_ph)):
+                if target is None:
+                    continue
+                dU = scipy.linalg.expm_frechet(-1j * tau * Hs[k], -1j * tau * G, compute_expm=False)
+                g = 2.0 * np.real(np.vdot(lam, dU @ psis[k]))
+                row = 0 if target.shape[0] == 1 else i
+                target[row, lo] += 0.5 * g
+                target[row, hi] += 0.5 * g
+        lam = Us[k].conj().T @ lam
+    return value, d_om, d_de, d_ph

@@ -436,3 +436,101 @@ def test_correlations_and_energy_moments():
     # one atom from |0>: H|0> = Omega/2 |1>
     E1, E2 = O.energy_moments(np.array([1.0, 0.0]), np.zeros((1, 1)), np.array([3.0]), np.array([1.5]))
     assert abs(E1) < 1e-15 and abs(E2 - 9.0 / 4.0) < 1e-14
+
+
+# ---------------------------------------------------------------------------
+# Overlap and gradients (Sec. III results; Sec. V: differentiability)
+# ---------------------------------------------------------------------------
+
+def test_overlap_of_product_states():
+    """<a|b> of two product states is the product of the single-atom overlaps."""
+    rng = np.random.default_rng(41)
+    n = 6
+    a1 = rng.normal(size=(n, 2)) + 1j * rng.normal(size=(n, 2))
+    b1 = rng.normal(size=(n, 2)) + 1j * rng.normal(size=(n, 2))
+    a, b = np.ones(1, complex), np.ones(1, complex)
+    for i in range(n):
+        a, b = np.kron(a, a1[i]), np.kron(b, b1[i])
+    ov, aa, bb = O.overlap(a, b)
+    want = np.prod([np.conj(a1[i]) @ b1[i] for i in range(n)])
+    assert abs(ov - want) <= 1e-12 * abs(want)
+    assert abs(aa - np.prod([np.sum(np.abs(a1[i]) ** 2) for i in range(n)])) <= 1e-12 * aa
+    assert abs(bb - np.prod([np.sum(np.abs(b1[i]) ** 2) for i in range(n)])) <= 1e-12 * bb
+
+
+def _gradient_case(seed, n, t_ns, dt, phi_rows):
+    rng = np.random.default_rng(seed)
+    pos = np.array([[0.0, 0.0], [6.0, 0.0], [3.0, 5.5], [9.0, 5.0]])[:n]
+    om = rng.uniform(2, 10, (n, t_ns))
+    de = rng.normal(0, 5, (1, t_ns))
+    ph = None if phi_rows == 0 else rng.uniform(-1, 1, (phi_rows, t_ns))
+    w = rng.normal(size=n)
+    return pos, om, de, ph, w
+
+
+@pytest.mark.parametrize("seed,n,t_ns,dt,phi_rows", [(5, 3, 47, 10, 3), (6, 4, 36, 7, 1), (7, 2, 30, 10, 0)])
+def test_gradient_matches_finite_differences(seed, n, t_ns, dt, phi_rows):
+    """Central differences of the dense forward evolution, on every sample the
+    midpoint rule reads (the others have zero gradient on both sides)."""
+    pos, om, de, ph, w = _gradient_case(seed, n, t_ns, dt, phi_rows)
+    c6 = W.C6_DEFAULT
+    B = O.occupation_bits(n)
+
+    def value(om_, de_, ph_):
+        psi, _ = O.evolve(pos, c6, t_ns, dt, om_, de_, ph_, method="dense", record_occupations=False)
+        return float(np.real(np.vdot(psi, (B @ w) * psi)))
+
+    v, d_om, d_de, d_ph = O.occupation_gradient(pos, c6, t_ns, dt, om, de, ph, w)
+    assert abs(v - value(om, de, ph)) <= 1e-13
+    used = sorted({x for s in O.step_schedule(t_ns, dt) for x in O.midpoint_samples(t_ns, *s)})
+    unused = [x for x in range(t_ns) if x not in used]
+    h = 1e-5
+    for name, arr, grad in (("om", om, d_om), ("de", de, d_de), ("ph", ph, d_ph)):
+        if arr is None:
+            assert grad is None
+            continue
+        assert np.all(grad[:, unused] == 0.0)
+        for r in range(arr.shape[0]):
+            for s in used[r % 2::2]:
+                a, b = arr.copy(), arr.copy()
+                a[r, s] += h
+                b[r, s] -= h
+                pick = lambda x: (x if name == "om" else om, x if name == "de" else de, x if name == "ph" else ph)
+                fd = (value(*pick(a)) - value(*pick(b))) / (2 * h)
+                assert abs(grad[r, s] - fd) <= 2e-9 * max(1.0, abs(fd)), (name, r, s, grad[r, s], fd)
+
+
+def test_gradient_single_atom_resonant_closed_form():
+    """One atom on resonance (delta = phi = 0) from |0>: the drive is a rotation
+    about x by theta = sum_k Omega_bar_k tau_k, so P1 = sin^2(theta / 2),
+    dP1/dOmega_bar_k = tau_k sin(theta) / 2, and every delta-derivative is zero
+    (the first-order change of the amplitude <1|U|0> is real while the
+    amplitude itself is imaginary)."""
+    rng = np.random.default_rng(1)
+    t_ns, dt = 53, 10
+    om = rng.uniform(1, 8, (1, t_ns))
+    de = np.zeros((1, t_ns))
+    v, d_om, d_de, _ = O.occupation_gradient([[0.0, 0.0]], 1.0, t_ns, dt, om, de)
+    sched = O.step_schedule(t_ns, dt)
+    bars = [0.5 * (om[0, lo] + om[0, hi]) for lo, hi in (O.midpoint_samples(t_ns, *s) for s in sched)]
+    theta = sum(b * s[1] / 1000.0 for b, s in zip(bars, sched))
+    assert abs(v - math.sin(theta / 2) ** 2) <= 1e-14
+    want = np.zeros_like(om)
+    for s in sched:
+        lo, hi = O.midpoint_samples(t_ns, *s)
+        g = (s[1] / 1000.0) * math.sin(theta) / 2
+        want[0, lo] += 0.5 * g
+        want[0, hi] += 0.5 * g
+    assert np.max(np.abs(d_om - want)) <= 1e-14
+    assert np.max(np.abs(d_de)) <= 1e-15
+
+
+def test_gradient_uniform_phase_sum_rule():
+    """A phase shared by all atoms and constant in time is a gauge from |0...0>:
+    the observable does not depend on it, so its sample derivatives sum to 0
+    (while individual samples need not vanish)."""
+    pos, om, de, _, w = _gradient_case(9, 3, 40, 10, 0)
+    ph = np.full((1, 40), 0.7)
+    _, _, _, d_ph = O.occupation_gradient(pos, W.C6_DEFAULT, 40, 10, om, de, ph, w)
+    assert np.max(np.abs(d_ph)) > 1e-5
+    assert abs(d_ph.sum()) <= 1e-14
