@@ -362,6 +362,48 @@ RSV_API rsv_status rsv_run_shots(rsv_ctx* ctx, const rsv_problem* problem, const
                                  const double* omega_scale, const double* delta_shift, const double* pos_shift_um,
                                  double* occ_mean, int32_t capacity_rows, int32_t* n_rows);
 
+/* ---- fidelity and gradients ------------------------------------------------ */
+
+/* Overlap of two device states (Sec. III results: fidelity with a target):
+ * out[0] + i out[1] = <a|b> = sum_b conj(a_b) b_b, out[2] = |a|^2,
+ * out[3] = |b|^2, accumulated to FP64-class accuracy (host array of 4). The
+ * fidelity is (out[0]^2 + out[1]^2) / (out[2] out[3]). a_dev, b_dev: 2^n_atoms
+ * amplitudes in `precision`, 16-byte aligned, caller-owned, only read.
+ * Synchronises the context stream. */
+RSV_API rsv_status rsv_overlap(rsv_ctx* ctx, int32_t n_atoms, int32_t precision, const void* a_dev,
+                               const void* b_dev, double* out);
+
+/* Value and gradient of an occupation observable at the end of the sequence,
+ * <O>(T) = <psi_K| sum_i weights[i] n_i |psi_K> (psi_K unnormalised, as
+ * evolved), with respect to every pulse sample (Sec. V: the emulator's
+ * expectation values are differentiable with respect to the pulse tensors).
+ *
+ * Exact for the piecewise-constant evolution of Eq. (6) up to the Krylov
+ * tolerance and a quadrature error below 1e-13 relative: adjoint method, the
+ * costate and the state evolved backwards (as conjugated forward Lanczos
+ * steps under the phase-negated Hamiltonian) through each step, the Duhamel
+ * integral of each step by composite 8-point Gauss-Legendre.
+ *
+ * weights: [n_atoms] host array (atom order). panels: Gauss-Legendre panels
+ * per step, 0 = automatic (ceil(W tau / 4) with W the Gershgorin bound of the
+ * step's spectral width sum_{i<j} V_ij + sum |delta_i| + sum |Omega_i|), else
+ * 1 .. 4096 for every step. Outputs (host, overwritten): *value_out;
+ * d_omega [omega_rows][t_ns], d_delta [delta_rows][t_ns] and, when non-NULL
+ * and phi_rows > 0, d_phi [phi_rows][t_ns], shaped like the problem's pulse
+ * arrays (a one-row array is shared by all atoms, so its gradient sums over
+ * them; samples the midpoint rule never reads get 0). *nodes_out (nullable):
+ * quadrature nodes used; *stats_out (nullable): Krylov iterations and
+ * launches of the forward and backward sweeps.
+ *
+ * Device memory from the context arena: the t_ns / dt_ns + 1 forward states
+ * (checkpoints) plus three solvers' footprints (the forward solver is freed
+ * before the two backward ones are made); RSV_ERR_OUT_OF_MEMORY when that
+ * does not fit. config->obs_stride is ignored. Synchronises the context
+ * stream. */
+RSV_API rsv_status rsv_gradient(rsv_ctx* ctx, const rsv_problem* problem, const rsv_config* config,
+                                const double* weights, int32_t panels, double* value_out, double* d_omega,
+                                double* d_delta, double* d_phi, int64_t* nodes_out, rsv_stats* stats_out);
+
 /* ---- serving: continuous admission of solves by device-memory footprint ------- */
 
 typedef struct {

@@ -476,6 +476,52 @@ def run_shots(ctx: Context, problem, dt_ns: int, omega_scale, delta_shift, pos_s
     return out
 
 
+def overlap(ctx: Context, n_atoms: int, precision, a, b) -> tuple[complex, float, float]:
+    """(<a|b>, |a|^2, |b|^2) of two CUDA state tensors (rsv_overlap)."""
+    out = np.empty(4)
+    check(L.lib().rsv_overlap(ctx.handle, int(n_atoms), precision_code(precision), _check_state(a, n_atoms, precision),
+                              _check_state(b, n_atoms, precision), L._dptr(out)))
+    return complex(out[0], out[1]), float(out[2]), float(out[3])
+
+
+def fidelity(ctx: Context, n_atoms: int, precision, target, psi) -> float:
+    """|<target|psi>|^2 / (|target|^2 |psi|^2)."""
+    ov, aa, bb = overlap(ctx, n_atoms, precision, target, psi)
+    return abs(ov) ** 2 / (aa * bb)
+
+
+class Gradient:
+    """Result of rsv_gradient: value = <sum_i w_i n_i>(T) and its derivatives
+    with respect to the pulse samples, shaped like the problem's arrays."""
+
+    def __init__(self, value, d_omega, d_delta, d_phi, nodes, stats):
+        self.value, self.d_omega, self.d_delta, self.d_phi = value, d_omega, d_delta, d_phi
+        self.nodes, self.stats = nodes, stats
+
+
+def gradient(ctx: Context, problem, dt_ns: int, weights, precision="c128", panels=0, krylov_tol=0.0, m_max=0,
+             max_substeps=0, initial_state=None) -> Gradient:
+    """rsv_gradient: d<O>(T)/d(pulse samples) for O = sum_i weights[i] n_i."""
+    init = None
+    if initial_state is not None:
+        init = np.ascontiguousarray(np.asarray(initial_state, dtype=amp_dtype(precision)))
+    pa = L.ProblemArgs.from_problem(problem, init)
+    cfg = L.make_config(dt_ns, precision, krylov_tol, m_max, max_substeps, 0)
+    w = np.ascontiguousarray(np.asarray(weights, dtype=np.float64))
+    if w.shape != (pa.n,):
+        raise ValueError("weights must have one entry per atom")
+    d_om, d_de = np.empty_like(pa.om), np.empty_like(pa.de)
+    d_ph = None if pa.ph is None else np.empty_like(pa.ph)
+    value = C.c_double()
+    nodes = C.c_int64()
+    st = L.Stats_()
+    check(L.lib().rsv_gradient(ctx.handle, C.byref(pa.struct), C.byref(cfg), L._dptr(w), int(panels),
+                               C.byref(value), L._dptr(d_om), L._dptr(d_de),
+                               L._dptr(d_ph) if d_ph is not None else C.POINTER(C.c_double)(),
+                               C.byref(nodes), C.byref(st)))
+    return Gradient(value.value, d_om, d_de, d_ph, nodes.value, {k: getattr(st, k) for k, _ in L.Stats_._fields_})
+
+
 def run(ctx: Context, problem, dt_ns: int, precision="c128", krylov_tol=0.0, m_max=0, max_substeps=0,
         obs_stride=1, initial_state=None) -> Result:
     """rsv_run: the whole sequence, host inputs in, a Result out."""

@@ -162,6 +162,18 @@ int batch_prepare(bool c64, int cluster, int* max_clusters);
 cudaError_t launch_dot3(const void* x, const void* y, int64_t dim, bool c64, double* partials, int grid,
                         cudaStream_t stream);
 
+// Pulse gradient and overlap (gradient_kernels.cu).
+// out_b = w(b) conj(in_b), w(b) = sum_q w_bits[q] b_q (bit order; NULL: 1).
+cudaError_t launch_conj_weight(const void* in, void* out, int64_t dim, bool c64, int n, const double* w_bits,
+                               int grid, cudaStream_t stream);
+// acc[q][0..5] += weight * (S0_q, S1_q, D_q as re/im pairs) of (mu, nu); a
+// grid of nchunks x n blocks; partials needs nchunks * n * 6 doubles.
+cudaError_t launch_generator(const void* mu, const void* nu, int64_t dim, bool c64, int n, int nchunks,
+                             double* partials, double weight, double* acc, cudaStream_t stream);
+// Per block Re<a, b>, Im<a, b>, |a|^2, |b|^2 (FP64-class), partials[grid][4].
+cudaError_t launch_overlap(const void* a, const void* b, int64_t dim, bool c64, double* partials, int grid,
+                           cudaStream_t stream);
+
 // Sampling (sample_kernels.cu)
 cudaError_t launch_block_sums(const void* psi, int64_t dim, bool c64, int64_t chunk, double* sums, cudaStream_t stream);
 cudaError_t launch_sample(const void* psi, int64_t dim, bool c64, int64_t chunk, const double* chunk_cdf, int64_t nchunks,

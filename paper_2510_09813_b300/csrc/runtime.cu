@@ -12,6 +12,7 @@
 #include <atomic>
 #include <chrono>
 #include <cmath>
+#include <complex>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -638,9 +639,10 @@ struct rsv_solver {
     return RSV_OK;
   }
 
-  rsv_status step_once() {
-    const int k = done;
-    const double tau = h_sp[k].tau;
+  // d_psi <- exp(-i tau H_k) d_psi under the parameters of step k (tau > 0,
+  // in us; Krylov restarts as needed). d_cpart must hold the observation
+  // partials of d_psi (left by the previous combine or observation).
+  rsv_status evolve(int k, double tau) {
     RSV_TRY(begin(tau, 0, nullptr));
     RSV_TRY(launch(RSV_KERNEL_CONTROL, 0.0, [&] {
       return launch_diag_table(d_sp + k, d_vmat, n, plan.a.L, plan.a.num_tiles, d_diag, stream);
@@ -683,6 +685,12 @@ struct rsv_solver {
       stats.substeps += 1;
       RSV_TRY(begin(0.0, 0, nullptr));
     }
+    return RSV_OK;
+  }
+
+  rsv_status step_once() {
+    const int k = done;
+    RSV_TRY(evolve(k, h_sp[k].tau));
     ++done;
     stats.steps += 1;
     const bool rec = (cfg.obs_stride > 0 && done % cfg.obs_stride == 0) || done == nsteps;
@@ -2033,6 +2041,290 @@ extern "C" rsv_status rsv_run_shots(rsv_ctx* ctx, const rsv_problem* problem, co
   *n_rows = got_rows;
   const int r = std::min(capacity_rows, got_rows);
   for (size_t i = 0; i < (size_t)r * n; ++i) occ_mean[i] = sum[i] / shots;
+  return RSV_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Pulse gradients (Sec. V: expectation values are differentiable with respect
+// to the tensors that define the pulses), by the adjoint method.
+//
+// With psi_{k+1} = U_k psi_k, U_k = exp(-i tau_k H_k) (Eq. (6)) and an
+// occupation observable O = sum_i w_i n_i, a parameter theta of H_k moves
+// <O>(T) by 2 Re <lambda_{k+1}| dU_k/dtheta |psi_k>, lambda_K = O psi_K,
+// lambda_k = U_k^dagger lambda_{k+1}. Duhamel's formula
+//     dU_k/dtheta = -i int_0^tau U_k(tau - s) G U_k(s) ds,  G = dH_k/dtheta,
+// turns it into 2 Im int_0^tau <lambda(s)| G |psi(s)> ds with lambda(s) and
+// psi(s) both evolved from step k + 1 back to time s of step k. Conjugation
+// makes those backward evolutions forward ones under conj(H_k) (H_k with the
+// phases negated), so they run on the ordinary Lanczos path:
+//     mu(s) = conj(lambda(s)) = exp(-i conj(H_k) (tau - s)) mu_{k+1},
+//     nu(s) = conj(psi(s))    = exp(-i conj(H_k) (tau - s)) conj(psi_{k+1}).
+// The integral is a composite Gauss-Legendre rule, 8 nodes per panel, taken
+// from s = tau down to 0 in one sweep of both vectors; the forward states
+// psi_k are kept (checkpoints) so nu restarts exactly at every step.
+//
+// Panels: for f(s) = <lambda_k| e^{iHs} G e^{-iHs} |psi_k> the 2Q-th
+// derivative is bounded by W^{2Q} |G| |lambda| |psi|, W the spectral width of
+// H_k (|ad_H| = W). The Q-point Gauss-Legendre error on a panel of width h is
+// h^{2Q+1} (Q!)^4 / ((2Q + 1) ((2Q)!)^3) times that bound, about
+// 1.7e-23 (W h)^16 relative for Q = 8, below 1e-13 while W h <= 4. W is bounded
+// by Gershgorin: W <= sum_{i<j} V_ij + sum_i |delta_i| + sum_i |Omega_i|.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int kGradNodesPerPanel = 8;
+constexpr int kGradMaxPanels = 4096;
+
+// Gauss-Legendre nodes (ascending) and weights on [-1, 1]: Newton's method on
+// P_q from the three-term Legendre recurrence, with Tricomi's first guess.
+void gauss_legendre(int q, std::vector<double>& x, std::vector<double>& w) {
+  constexpr double kPi = 3.14159265358979323846;
+  x.assign(q, 0.0);
+  w.assign(q, 0.0);
+  for (int i = 0; i < q; ++i) {
+    double z = std::cos(kPi * (i + 0.75) / (q + 0.5));
+    double dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= q; ++k) {
+        const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = q == 1 ? 1.0 : q * (z * p1 - p0) / (z * z - 1.0);
+      const double dz = p1 / dp;
+      z -= dz;
+      if (std::fabs(dz) <= 1e-16) break;
+    }
+    x[q - 1 - i] = z;
+    w[q - 1 - i] = 2.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
+int gradient_panels(const StepParams& sp, const std::vector<double>& v_atoms, int n) {
+  double width = 0.0;
+  for (int i = 0; i < n; ++i)
+    for (int j = i + 1; j < n; ++j) width += std::fabs(v_atoms[(size_t)i * n + j]);
+  for (int q = 0; q < n; ++q) width += std::fabs(sp.delta[q]) + 2.0 * std::fabs(sp.half_omega[q]);
+  const double p = std::ceil(width * sp.tau / 4.0);
+  return (int)std::min<double>(kGradMaxPanels, std::max(1.0, p));
+}
+
+}  // namespace
+
+extern "C" rsv_status rsv_gradient(rsv_ctx* ctx, const rsv_problem* problem, const rsv_config* config,
+                                   const double* weights, int32_t panels, double* value_out, double* d_omega,
+                                   double* d_delta, double* d_phi, int64_t* nodes_out, rsv_stats* stats_out) {
+  g_last_error.clear();
+  if (!ctx || !config || !weights || !value_out || !d_omega || !d_delta) return fail(RSV_ERR_INVALID_ARG, "NULL argument");
+  RSV_TRY(validate_problem(problem));
+  if (panels < 0 || panels > kGradMaxPanels)
+    return fail(RSV_ERR_INVALID_ARG, "panels must be in [0, " + std::to_string(kGradMaxPanels) + "]");
+  if (config->dt_ns < 1) return fail(RSV_ERR_INVALID_ARG, "dt_ns must be >= 1");
+  const int n = problem->n_atoms, T = problem->t_ns;
+  rsv_config cfg = *config;
+  cfg.obs_stride = 0;
+  const int K = num_steps(T, cfg.dt_ns);
+  for (size_t i = 0; i < (size_t)problem->omega_rows * T; ++i) d_omega[i] = 0.0;
+  for (size_t i = 0; i < (size_t)problem->delta_rows * T; ++i) d_delta[i] = 0.0;
+  if (d_phi)
+    for (size_t i = 0; i < (size_t)problem->phi_rows * T; ++i) d_phi[i] = 0.0;
+  std::vector<double> v_atoms;
+  RSV_TRY(pair_energies(n, problem->dim, problem->positions_um, problem->c6, v_atoms));
+  std::vector<StepParams> sp;
+  RSV_TRY(step_params(problem, cfg.dt_ns, sp));
+
+  // everything the call holds on the device, released on every exit path
+  struct Held {
+    rsv_ctx* ctx;
+    std::vector<rsv_solver*> solvers;
+    std::vector<void*> bufs;
+    ~Held() {
+      for (rsv_solver* s : solvers) rsv_solver_destroy(s);
+      if (!bufs.empty()) cudaStreamSynchronize(ctx->stream);
+      for (void* p : bufs) ctx->arena.release(p);
+    }
+  } held{ctx, {}, {}};
+  auto alloc = [&](size_t bytes, void** p) -> rsv_status {
+    RSV_TRY(ctx->arena.alloc(bytes, p));
+    held.bufs.push_back(*p);
+    return RSV_OK;
+  };
+  const bool c64 = cfg.precision == RSV_C64;
+  const int64_t dim = int64_t(1) << n;
+  const size_t vbytes = (size_t)dim * amp_bytes(cfg.precision);
+  std::vector<void*> ckpt(K + 1, nullptr);
+  for (int k = 0; k <= K; ++k) {
+    const rsv_status st = alloc(vbytes, &ckpt[k]);
+    if (st != RSV_OK)
+      return fail(st, "gradient checkpoints (" + std::to_string(K + 1) + " states of " + std::to_string(vbytes) +
+                          " bytes) do not fit the arena");
+  }
+  const int64_t nvec = c64 ? dim / 2 : dim;
+  const int nchunks = (int)std::max<int64_t>(
+      1, std::min<int64_t>((nvec + kThreads - 1) / kThreads, (4 * ctx->num_sms + n - 1) / n));
+  double *d_acc = nullptr, *d_wbits = nullptr, *d_gpart = nullptr;
+  RSV_TRY(alloc(sizeof(double) * 6 * n, (void**)&d_acc));
+  RSV_TRY(alloc(sizeof(double) * n, (void**)&d_wbits));
+  RSV_TRY(alloc(sizeof(double) * 6 * n * (size_t)nchunks, (void**)&d_gpart));
+  std::vector<double> wbits(n);
+  for (int i = 0; i < n; ++i) wbits[n - 1 - i] = weights[i];  // atom i sits at bit n - 1 - i
+  rsv_stats total{};
+  auto add_stats = [&](const rsv_solver* s) {
+    total.krylov_iterations += s->stats.krylov_iterations;
+    total.substeps += s->stats.substeps;
+    total.kernel_launches += s->stats.kernel_launches;
+    total.max_error_estimate = std::max(total.max_error_estimate, s->stats.max_error_estimate);
+  };
+  const auto t0 = std::chrono::steady_clock::now();
+
+  // forward sweep, keeping psi_0 .. psi_K
+  rsv_solver* F = nullptr;
+  RSV_TRY(solver_create(ctx, problem, &cfg, nullptr, &F));
+  held.solvers.push_back(F);
+  double value = 0.0;
+  {
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    cudaSetDevice(ctx->device);
+    RSV_CUDA(cudaMemcpyAsync(d_wbits, wbits.data(), sizeof(double) * n, cudaMemcpyHostToDevice, F->stream));
+    RSV_CUDA(cudaMemcpyAsync(ckpt[0], F->d_psi, vbytes, cudaMemcpyDeviceToDevice, F->stream));
+    for (int k = 0; k < K; ++k) {
+      RSV_TRY(F->step_once());
+      RSV_CUDA(cudaMemcpyAsync(ckpt[k + 1], F->d_psi, vbytes, cudaMemcpyDeviceToDevice, F->stream));
+    }
+    std::vector<double> occ(n);
+    RSV_CUDA(cudaMemcpyAsync(occ.data(), F->d_occ + (size_t)(F->rows - 1) * n, sizeof(double) * n,
+                             cudaMemcpyDeviceToHost, F->stream));
+    RSV_CUDA(cudaStreamSynchronize(F->stream));
+    for (int i = 0; i < n; ++i) value += weights[i] * occ[i];
+  }
+  add_stats(F);
+  total.steps = K;
+  *value_out = value;
+  held.solvers.pop_back();
+  rsv_solver_destroy(F);
+
+  // backward sweep on the conjugated problem
+  std::vector<double> neg_phi;
+  rsv_problem back = *problem;
+  back.initial_state = nullptr;
+  if (problem->phi_rows > 0) {
+    neg_phi.assign(problem->phi, problem->phi + (size_t)problem->phi_rows * T);
+    for (double& v : neg_phi) v = -v;
+    back.phi = neg_phi.data();
+  }
+  rsv_solver *Bmu = nullptr, *Bnu = nullptr;
+  RSV_TRY(solver_create(ctx, &back, &cfg, nullptr, &Bmu));
+  held.solvers.push_back(Bmu);
+  RSV_TRY(solver_create(ctx, &back, &cfg, nullptr, &Bnu));
+  held.solvers.push_back(Bnu);
+  std::vector<double> gx, gw;
+  gauss_legendre(kGradNodesPerPanel, gx, gw);
+  int64_t nodes = 0, launches = 0;
+  {
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = ctx->stream;
+    const int grid = 4 * ctx->num_sms;
+    // mu_K = O conj(psi_K); a vanishing costate leaves every derivative zero
+    RSV_CUDA(launch_conj_weight(ckpt[K], Bmu->d_psi, dim, c64, n, d_wbits, grid, st));
+    launches += 1;
+    RSV_TRY(Bmu->observe_into_partials());
+    RSV_TRY(Bmu->begin(0.0, 1, nullptr));
+    RSV_TRY(Bmu->read_status());
+    const bool live = Bmu->h_ks->norm2 > 0.0;
+    std::vector<double> acc(6 * n);
+    for (int k = K - 1; k >= 0 && live; --k) {
+      const double tau = sp[k].tau;
+      const int P = panels > 0 ? panels : gradient_panels(sp[k], v_atoms, n);
+      // nodes s_j and weights w_j of the composite rule on [0, tau], ascending
+      std::vector<double> s, w;
+      for (int p = 0; p < P; ++p) {
+        const double a = tau * p / P, h = tau / P;
+        for (int j = 0; j < kGradNodesPerPanel; ++j) {
+          s.push_back(a + 0.5 * h * (1.0 + gx[j]));
+          w.push_back(0.5 * h * gw[j]);
+        }
+      }
+      nodes += (int64_t)s.size();
+      RSV_CUDA(launch_conj_weight(ckpt[k + 1], Bnu->d_psi, dim, c64, n, nullptr, grid, st));
+      launches += 1 + 2 * (int64_t)s.size();
+      RSV_TRY(Bnu->observe_into_partials());
+      RSV_CUDA(cudaMemsetAsync(d_acc, 0, sizeof(double) * 6 * n, st));
+      double at = tau;
+      for (int j = (int)s.size() - 1; j >= 0; --j) {
+        const double step = at - s[j];
+        if (step > 0.0) {
+          RSV_TRY(Bmu->evolve(k, step));
+          RSV_TRY(Bnu->evolve(k, step));
+        }
+        at = s[j];
+        RSV_CUDA(launch_generator(Bmu->d_psi, Bnu->d_psi, dim, c64, n, nchunks, d_gpart, w[j], d_acc, st));
+      }
+      if (at > 0.0) RSV_TRY(Bmu->evolve(k, at));  // mu_k, the next step's costate
+      RSV_CUDA(cudaMemcpyAsync(acc.data(), d_acc, sizeof(double) * 6 * n, cudaMemcpyDeviceToHost, st));
+      RSV_CUDA(cudaStreamSynchronize(st));
+      // the step's samples under the midpoint rule, weight 1/2 each
+      const int start = k * cfg.dt_ns, len = std::min(cfg.dt_ns, T - start);
+      const int twice_m = 2 * start + len;
+      const int lo = std::min(twice_m / 2, T - 1), hi = std::min((twice_m + 1) / 2, T - 1);
+      for (int i = 0; i < n; ++i) {
+        const int q = n - 1 - i;
+        const std::complex<double> s0(acc[6 * q + 0], acc[6 * q + 1]), s1(acc[6 * q + 2], acc[6 * q + 3]),
+            dd(acc[6 * q + 4], acc[6 * q + 5]);
+        const double phase = sp[k].phi[q], om = 2.0 * sp[k].half_omega[q];
+        const std::complex<double> e(std::cos(phase), std::sin(phase)), I(0.0, 1.0);
+        // <0|dh/dOmega|1> = e/2, <1|dh/dOmega|0> = conj(e)/2; dh/ddelta = -n;
+        // <0|dh/dphi|1> = i Omega/2 e, <1|dh/dphi|0> = -i Omega/2 conj(e)
+        const double g_om = 2.0 * std::imag(0.5 * e * s0 + 0.5 * std::conj(e) * s1);
+        const double g_de = 2.0 * std::imag(-dd);
+        const double g_ph = 2.0 * std::imag(I * (0.5 * om) * (e * s0 - std::conj(e) * s1));
+        double* ro = d_omega + (size_t)(problem->omega_rows == 1 ? 0 : i) * T;
+        double* rd = d_delta + (size_t)(problem->delta_rows == 1 ? 0 : i) * T;
+        ro[lo] += 0.5 * g_om;
+        ro[hi] += 0.5 * g_om;
+        rd[lo] += 0.5 * g_de;
+        rd[hi] += 0.5 * g_de;
+        if (d_phi && problem->phi_rows > 0) {
+          double* rp = d_phi + (size_t)(problem->phi_rows == 1 ? 0 : i) * T;
+          rp[lo] += 0.5 * g_ph;
+          rp[hi] += 0.5 * g_ph;
+        }
+      }
+    }
+  }
+  add_stats(Bmu);
+  add_stats(Bnu);
+  total.kernel_launches += launches;
+  total.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  total.tile_passes = Bmu->plan.two_pass ? 2 : 1;
+  total.krylov_dim_max = cfg.m_max;
+  if (nodes_out) *nodes_out = nodes;
+  if (stats_out) *stats_out = total;
+  return RSV_OK;
+}
+
+// Overlap <a|b> with |a|^2 and |b|^2 (fidelity with a target state).
+extern "C" rsv_status rsv_overlap(rsv_ctx* ctx, int32_t n_atoms, int32_t precision, const void* a_dev,
+                                  const void* b_dev, double* out) {
+  g_last_error.clear();
+  if (!ctx || !a_dev || !b_dev || !out) return fail(RSV_ERR_INVALID_ARG, "NULL argument");
+  if (n_atoms < 1 || n_atoms > 31) return fail(RSV_ERR_INVALID_ARG, "n_atoms out of range");
+  if (precision != RSV_C64 && precision != RSV_C128) return fail(RSV_ERR_INVALID_ARG, "bad precision");
+  if ((reinterpret_cast<uintptr_t>(a_dev) | reinterpret_cast<uintptr_t>(b_dev)) & 15)
+    return fail(RSV_ERR_INVALID_ARG, "states must be 16-byte aligned");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  cudaSetDevice(ctx->device);
+  const int grid = 4 * ctx->num_sms;
+  RSV_CUDA(launch_overlap(a_dev, b_dev, int64_t(1) << n_atoms, precision == RSV_C64, ctx->d_part, grid, ctx->stream));
+  std::vector<double> part((size_t)grid * 4);
+  RSV_CUDA(cudaMemcpyAsync(part.data(), ctx->d_part, part.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                           ctx->stream));
+  RSV_CUDA(cudaStreamSynchronize(ctx->stream));
+  double sum[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int b = 0; b < grid; ++b)
+    for (int v = 0; v < 4; ++v) sum[v] += part[(size_t)b * 4 + v];
+  for (int v = 0; v < 4; ++v) out[v] = sum[v];
   return RSV_OK;
 }
 

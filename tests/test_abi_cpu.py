@@ -112,3 +112,17 @@ def test_new_entries_reject_bad_arguments_without_a_gpu():
     assert lib.rsv_observe_static(4, L.RSV_C64, None, None, None) == -1
     assert lib.rsv_observe_static(32, L.RSV_C64, C.c_void_p(16), C.c_void_p(16), None) == -1
     assert b"limit of 31 atoms" in lib.rsv_last_error()
+
+
+def test_overlap_and_gradient_reject_bad_arguments_without_a_gpu():
+    lib = L.lib()
+    out = np.zeros(4)
+    assert lib.rsv_overlap(None, 4, L.RSV_C64, None, None, L._dptr(out)) == -1
+    pa = L.ProblemArgs([[0.0, 0.0], [6.0, 0.0]], 5420158.53, 20, np.ones(20), np.zeros(20))
+    cfg = L.make_config(10, "c128", 0.0, 0, 0, 0)
+    w = np.ones(2)
+    v = C.c_double()
+    d_om, d_de = np.zeros((1, 20)), np.zeros((1, 20))
+    assert lib.rsv_gradient(None, C.byref(pa.struct), C.byref(cfg), L._dptr(w), 0, C.byref(v), L._dptr(d_om),
+                            L._dptr(d_de), None, None, None) == -1
+    assert b"NULL" in lib.rsv_last_error()
