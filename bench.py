@@ -299,6 +299,33 @@ def serving_leg(api, W, device: int, count: int, n_hi: int):
             "one_at_a_time_c128": {"slots": 1, **fifo}}
 
 
+GRADIENT_WORKLOAD = ("8-atom chain at 6 um, Omega = 2*pi rad/us, delta = 0, first 300 ns of the sequence, "
+                     "dt = 10 ns, complex128; d<sum_i n_i>(T)/d(Omega and delta samples)")
+
+
+def gradient_leg(api, W, device: int):
+    """Pulse gradient of the total Rydberg population by the adjoint method,
+    timed beside the plain forward solve of the same problem."""
+    prob = W.rabi_chain(t_ns=300)
+    ctx = api.Context(device)
+    w = np.ones(8)
+    api.gradient(ctx, prob, 10, w, precision="c128")  # warm-up
+    t0 = time.perf_counter()
+    g = api.gradient(ctx, prob, 10, w, precision="c128")
+    grad_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    r = api.run(ctx, prob, 10, "c128", obs_stride=0)
+    fwd_s = time.perf_counter() - t0
+    r.close()
+    ctx.close()
+    steps = g.stats["steps"]
+    return {"workload": GRADIENT_WORKLOAD, "seconds": grad_s, "forward_seconds": fwd_s,
+            "ratio_to_forward": grad_s / fwd_s, "quadrature_nodes": g.nodes,
+            "nodes_per_step": g.nodes / steps, "krylov_iterations": g.stats["krylov_iterations"],
+            "kernel_launches": g.stats["kernel_launches"], "value": g.value,
+            "sample_derivatives_per_s": (g.d_omega.size + g.d_delta.size) / grad_s}
+
+
 # ---------------------------------------------------------------------------
 # Our arm
 # ---------------------------------------------------------------------------
@@ -441,6 +468,7 @@ def ours(args):
     batched = None if args.no_batch else batched_leg(api, W, local)
     serving = None if args.serve_requests <= 0 else serving_leg(api, W, local, args.serve_requests,
                                                                 args.serve_max_atoms)
+    gradient = None if args.no_gradient else gradient_leg(api, W, local)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -481,6 +509,7 @@ def ours(args):
             "cpu_baseline": cpu,
             "batched": batched,
             "serving": serving,
+            "gradient": gradient,
         }
         print(json.dumps(line))
     if ws > 1:
@@ -540,6 +569,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 512-register batched leg")
+    ap.add_argument("--no-gradient", action="store_true", help="skip the pulse-gradient leg")
     ap.add_argument("--serve-requests", type=int, default=SERVE_REQUESTS,
                     help="requests of the serving leg (0 skips it)")
     ap.add_argument("--serve-max-atoms", type=int, default=SERVE_MAX_ATOMS,
