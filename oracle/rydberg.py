@@ -541,3 +541,72 @@ def occupation_gradient(positions, c6, t_ns, dt_ns, omega, delta, phi=None, weig
                 target[row, hi] += 0.5 * g
         lam = Us[k].conj().T @ lam
     return value, d_om, d_de, d_ph
+
+
+# ---------------------------------------------------------------------------
+# Open-system dynamics: the Lindblad master equation (Sec. III.A), dense.
+# ---------------------------------------------------------------------------
+# Reading of the noise channels, which the paper names without operators:
+# per atom i, Rydberg dephasing L = sqrt(g_deph_i) n_i and spontaneous decay
+# L = sqrt(g_relax_i) |0><1|_i, rates in 1/us.
+#     d rho/dt = -i [H, rho] + sum_L (L rho L^dag - {L^dag L, rho} / 2)
+# rho is stored row-major, vec(rho)[r * 2^N + c] = rho[r, c], so that
+# vec(A rho B) = (A kron B^T) vec(rho).
+
+
+def jump_operators(n_atoms: int, g_deph, g_relax):
+    """The list of dense jump operators of the two channels (zero rates omitted)."""
+    D = 2 ** n_atoms
+    ops = []
+    for i in range(n_atoms):
+        bit = atom_bit(n_atoms, i)
+        if g_deph[i] > 0.0:
+            L = np.zeros((D, D), dtype=np.complex128)
+            for b in range(D):
+                if (b >> bit) & 1:
+                    L[b, b] = math.sqrt(g_deph[i])
+            ops.append(L)
+        if g_relax[i] > 0.0:
+            L = np.zeros((D, D), dtype=np.complex128)
+            for b in range(D):
+                if (b >> bit) & 1:  # |1> -> |0> on atom i
+                    L[b ^ (1 << bit), b] = math.sqrt(g_relax[i])
+            ops.append(L)
+    return ops
+
+
+def liouvillian(H, jumps) -> np.ndarray:
+    """Dense superoperator of the master equation on row-major vec(rho)."""
+    D = H.shape[0]
+    I = np.eye(D)
+    Lv = -1j * (np.kron(H, I) - np.kron(I, H.T))
+    for L in jumps:
+        LdL = L.conj().T @ L
+        Lv += np.kron(L, L.conj()) - 0.5 * (np.kron(LdL, I) + np.kron(I, LdL.T))
+    return Lv
+
+
+def lindblad_evolve(positions, c6, t_ns, dt_ns, omega, delta, phi=None, g_deph=None, g_relax=None, rho0=None,
+                    record_occupations: bool = True):
+    """rho_K = exp(tau L_{K-1}) ... exp(tau L_0) rho_0 with the midpoint pulses of
+    Sec. III held over each step (brute force, N <= 5). rho_0 defaults to
+    |0...0><0...0|. Returns (rho_K [D][D], occ) with occ[k][i] = tr(rho_k n_i)."""
+    V = pair_interactions(positions, c6)
+    n = V.shape[0]
+    D = 2 ** n
+    gd = np.zeros(n) if g_deph is None else np.asarray(g_deph, dtype=np.float64)
+    gr = np.zeros(n) if g_relax is None else np.asarray(g_relax, dtype=np.float64)
+    jumps = jump_operators(n, gd, gr)
+    if rho0 is None:
+        rho = np.zeros((D, D), dtype=np.complex128)
+        rho[0, 0] = 1.0
+    else:
+        rho = np.array(rho0, dtype=np.complex128).reshape(D, D)
+    B = occupation_bits(n)
+    occ = [np.real(np.diag(rho)) @ B] if record_occupations else []
+    for tau, om, de, ph in step_parameters(n, t_ns, dt_ns, omega, delta, phi):
+        Lv = liouvillian(dense_hamiltonian(V, om, de, ph), jumps)
+        rho = (scipy.linalg.expm(tau * Lv) @ rho.reshape(-1)).reshape(D, D)
+        if record_occupations:
+            occ.append(np.real(np.diag(rho)) @ B)
+    return rho, np.array(occ)

@@ -534,3 +534,64 @@ def test_gradient_uniform_phase_sum_rule():
     _, _, _, d_ph = O.occupation_gradient(pos, W.C6_DEFAULT, 40, 10, om, de, ph, w)
     assert np.max(np.abs(d_ph)) > 1e-5
     assert abs(d_ph.sum()) <= 1e-14
+
+
+# ---------------------------------------------------------------------------
+# Lindblad master equation (Sec. III.A: open-system dynamics)
+# ---------------------------------------------------------------------------
+
+def test_lindblad_without_noise_is_the_pure_state():
+    """Zero rates: rho(T) = psi(T) psi(T)^dag of the (pinned) pure-state evolution."""
+    rng = np.random.default_rng(2)
+    n, t = 3, 60
+    pos = np.array([[0.0, 0.0], [6.0, 0.0], [3.0, 5.5]])
+    om, de, ph = rng.uniform(2, 10, (n, t)), rng.normal(0, 5, (1, t)), rng.uniform(-1, 1, (n, t))
+    rho, occ = O.lindblad_evolve(pos, W.C6_DEFAULT, t, 10, om, de, ph)
+    psi, occ2 = O.evolve(pos, W.C6_DEFAULT, t, 10, om, de, ph, method="dense")
+    assert np.max(np.abs(rho - np.outer(psi, psi.conj()))) <= 1e-13
+    assert np.max(np.abs(occ - occ2)) <= 1e-13
+
+
+def test_lindblad_single_atom_closed_forms():
+    """Undriven atom: the excited population decays as e^{-g_r t}; the
+    coherence rho_01 turns at the detuning (E_1 = -delta) and decays at
+    (g_deph + g_relax) / 2."""
+    g = 0.7
+    rho, occ = O.lindblad_evolve([[0.0, 0.0]], 1.0, 2000, 50, np.zeros((1, 2000)), np.full((1, 2000), 3.0),
+                                 None, [0.0], [g], rho0=np.array([[0, 0], [0, 1]], complex))
+    assert abs(occ[-1, 0] - math.exp(-g * 2.0)) <= 1e-13
+    assert abs(occ[20, 0] - math.exp(-g * 1.0)) <= 1e-13
+    gd, gr, de, T = 0.4, 0.3, 2.0, 1500
+    rho, _ = O.lindblad_evolve([[0.0, 0.0]], 1.0, T, 30, np.zeros((1, T)), np.full((1, T), de), None, [gd], [gr],
+                               rho0=np.full((2, 2), 0.5, complex))
+    t = T / 1000
+    assert abs(rho[0, 1] - 0.5 * np.exp(-1j * de * t) * np.exp(-(gd + gr) * t / 2)) <= 1e-13
+    assert abs(rho[1, 1] - 0.5 * math.exp(-gr * t)) <= 1e-13
+
+
+def test_lindblad_driven_damped_steady_state():
+    """Resonance fluorescence: a driven atom with decay g settles at
+    rho_11 = (Omega^2 / 4) / (delta^2 + Omega^2 / 2 + g^2 / 4)."""
+    Om, dl, g, T = 3.0, 1.5, 2.0, 20000
+    _, occ = O.lindblad_evolve([[0.0, 0.0]], 1.0, T, 100, np.full((1, T), Om), np.full((1, T), dl), None,
+                               [0.0], [g])
+    assert abs(occ[-1, 0] - (Om ** 2 / 4) / (dl ** 2 + Om ** 2 / 2 + g ** 2 / 4)) <= 1e-9
+
+
+def test_lindblad_state_stays_a_density_matrix():
+    """Trace 1, Hermitian and positive semidefinite at every step, with both
+    channels on three interacting atoms."""
+    rng = np.random.default_rng(8)
+    n, t = 3, 40
+    pos = np.array([[0.0, 0.0], [6.0, 0.0], [3.0, 5.5]])
+    om, de = rng.uniform(2, 10, (1, t)), rng.normal(0, 5, (n, t))
+    V = O.pair_interactions(pos, W.C6_DEFAULT)
+    jumps = O.jump_operators(n, [0.5, 0.0, 1.0], [0.3, 0.8, 0.0])
+    rho = np.zeros((8, 8), complex)
+    rho[0, 0] = 1.0
+    for tau, o, d, p in O.step_parameters(n, t, 10, om, de, None):
+        rho = (scipy.linalg.expm(tau * O.liouvillian(O.dense_hamiltonian(V, o, d, p), jumps)) @ rho.reshape(-1)
+               ).reshape(8, 8)
+        assert abs(np.trace(rho) - 1.0) <= 1e-13
+        assert np.max(np.abs(rho - rho.conj().T)) <= 1e-14
+        assert np.min(np.linalg.eigvalsh(0.5 * (rho + rho.conj().T))) >= -1e-13
