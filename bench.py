@@ -326,6 +326,28 @@ def gradient_leg(api, W, device: int):
             "sample_derivatives_per_s": (g.d_omega.size + g.d_delta.size) / grad_s}
 
 
+LINDBLAD_WORKLOAD = ("10-atom chain at 6 um, Omega = 2*pi rad/us, delta = 0, Rydberg dephasing 0.2/us and decay "
+                     "0.1/us on every atom, first 300 ns, dt = 10 ns; rho of 4^10 complex128 amplitudes")
+
+
+def lindblad_leg(api, W, device: int):
+    """Lindblad evolution of a 10-atom chain (Arnoldi on vec(rho))."""
+    prob = W.rabi_chain(n=10, t_ns=300)
+    ctx = api.Context(device)
+    g_d, g_r = np.full(10, 0.2), np.full(10, 0.1)
+    api.lindblad_run(ctx, W.rabi_chain(n=10, t_ns=20), 10, g_d, g_r, obs_stride=0)  # warm-up
+    t0 = time.perf_counter()
+    res = api.lindblad_run(ctx, prob, 10, g_d, g_r, obs_stride=0)
+    sec = time.perf_counter() - t0
+    ctx.close()
+    st = res.stats
+    return {"workload": LINDBLAD_WORKLOAD, "seconds": sec, "steps_per_s": st["steps"] / sec,
+            "krylov_iterations_per_step": st["krylov_iterations"] / st["steps"],
+            "krylov_iterations_per_s": st["krylov_iterations"] / sec, "substeps": st["substeps"],
+            "kernel_launches": st["kernel_launches"], "trace": float(np.trace(res.rho).real),
+            "rydberg_population": float(res.occupations[-1].sum())}
+
+
 # ---------------------------------------------------------------------------
 # Our arm
 # ---------------------------------------------------------------------------
@@ -469,6 +491,7 @@ def ours(args):
     serving = None if args.serve_requests <= 0 else serving_leg(api, W, local, args.serve_requests,
                                                                 args.serve_max_atoms)
     gradient = None if args.no_gradient else gradient_leg(api, W, local)
+    lindblad = None if args.no_lindblad else lindblad_leg(api, W, local)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -510,6 +533,7 @@ def ours(args):
             "batched": batched,
             "serving": serving,
             "gradient": gradient,
+            "lindblad": lindblad,
         }
         print(json.dumps(line))
     if ws > 1:
@@ -570,6 +594,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 512-register batched leg")
     ap.add_argument("--no-gradient", action="store_true", help="skip the pulse-gradient leg")
+    ap.add_argument("--no-lindblad", action="store_true", help="skip the Lindblad leg")
     ap.add_argument("--serve-requests", type=int, default=SERVE_REQUESTS,
                     help="requests of the serving leg (0 skips it)")
     ap.add_argument("--serve-max-atoms", type=int, default=SERVE_MAX_ATOMS,

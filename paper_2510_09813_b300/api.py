@@ -522,6 +522,48 @@ def gradient(ctx: Context, problem, dt_ns: int, weights, precision="c128", panel
     return Gradient(value.value, d_om, d_de, d_ph, nodes.value, {k: getattr(st, k) for k, _ in L.Stats_._fields_})
 
 
+class LindbladResult:
+    """Result of rsv_lindblad_run: the final density matrix, the occupation
+    rows tr(rho n_i) and the run's statistics."""
+
+    def __init__(self, rho, occupations, stats):
+        self.rho, self.occupations, self.stats = rho, occupations, stats
+
+
+def lindblad_run(ctx: Context, problem, dt_ns: int, g_dephasing=None, g_relaxation=None, rho0=None,
+                 krylov_tol=0.0, m_max=0, max_substeps=0, obs_stride=1) -> LindbladResult:
+    """rsv_lindblad_run: the Lindblad master equation with per-atom Rydberg
+    dephasing and spontaneous decay rates (1/us), complex128."""
+    pa = L.ProblemArgs.from_problem(problem)
+    n = pa.n
+    cfg = L.make_config(dt_ns, "c128", krylov_tol, m_max, max_substeps, obs_stride)
+
+    def rates(g):
+        if g is None:
+            return None
+        g = np.ascontiguousarray(np.asarray(g, dtype=np.float64))
+        if g.shape != (n,):
+            raise ValueError("rates must have one entry per atom")
+        return g
+
+    gd, gr = rates(g_dephasing), rates(g_relaxation)
+    r0 = None
+    if rho0 is not None:
+        r0 = np.ascontiguousarray(np.asarray(rho0, dtype=np.complex128))
+        if r0.shape != (2 ** n, 2 ** n):
+            raise ValueError("rho0 must be [2^n][2^n]")
+    nulld = C.POINTER(C.c_double)()
+    rows = C.c_int32()
+    args = (ctx.handle, C.byref(pa.struct), C.byref(cfg), L._dptr(gd) if gd is not None else nulld,
+            L._dptr(gr) if gr is not None else nulld, None if r0 is None else r0.ctypes.data)
+    check(L.lib().rsv_lindblad_run(*args, None, nulld, 0, C.byref(rows), None))
+    rho = np.empty((2 ** n, 2 ** n), dtype=np.complex128)
+    occ = np.empty((rows.value, n))
+    st = L.Stats_()
+    check(L.lib().rsv_lindblad_run(*args, rho.ctypes.data, L._dptr(occ), rows.value, C.byref(rows), C.byref(st)))
+    return LindbladResult(rho, occ[:rows.value], {k: getattr(st, k) for k, _ in L.Stats_._fields_})
+
+
 def run(ctx: Context, problem, dt_ns: int, precision="c128", krylov_tol=0.0, m_max=0, max_substeps=0,
         obs_stride=1, initial_state=None) -> Result:
     """rsv_run: the whole sequence, host inputs in, a Result out."""

@@ -174,6 +174,27 @@ cudaError_t launch_generator(const void* mu, const void* nu, int64_t dim, bool c
 cudaError_t launch_overlap(const void* a, const void* b, int64_t dim, bool c64, double* partials, int grid,
                            cudaStream_t stream);
 
+// Lindblad master equation on vec(rho), complex128 (lindblad_kernels.cu).
+constexpr int kLindbladMaxAtoms = 14;   // vec(rho) of 4^14 amplitudes (4 GiB)
+constexpr int kLindbladMaxKrylov = 64;  // Arnoldi basis vectors
+struct LindbladParams {
+  int n;
+  // by bit q: <0|h_q|1> = Omega_q/2 e^{+i phi_q} (re, im), dephasing and decay rates (1/us)
+  double hre[kLindbladMaxAtoms], him[kLindbladMaxAtoms];
+  double gd[kLindbladMaxAtoms], gr[kLindbladMaxAtoms];
+};
+// y = L(x); E: [2^n] diagonal energies by bit-order index.
+cudaError_t launch_lindblad_apply(const void* x, void* y, const double* E, const LindbladParams& p, int grid,
+                                  cudaStream_t stream);
+// out[2k], out[2k+1] = Re, Im <V_k, w> for k < nvec (device array of nvec
+// device pointers); partials needs nchunks * nvec * 2 doubles.
+cudaError_t launch_multi_dot(const void* const* V, int nvec, const void* w, int64_t total, int nchunks,
+                             double* partials, double* out, cudaStream_t stream);
+// w = (overwrite ? 0 : w) - sum_k (coef[2k] + i coef[2k+1]) V_k; *norm2_out = |w|^2
+// (device); partials needs grid doubles.
+cudaError_t launch_multi_axpy(const void* const* V, const double* coef, int nvec, void* w, int64_t total,
+                              bool overwrite, int grid, double* partials, double* norm2_out, cudaStream_t stream);
+
 // Sampling (sample_kernels.cu)
 cudaError_t launch_block_sums(const void* psi, int64_t dim, bool c64, int64_t chunk, double* sums, cudaStream_t stream);
 cudaError_t launch_sample(const void* psi, int64_t dim, bool c64, int64_t chunk, const double* chunk_cdf, int64_t nchunks,

@@ -2329,6 +2329,311 @@ extern "C" rsv_status rsv_overlap(rsv_ctx* ctx, int32_t n_atoms, int32_t precisi
 }
 
 // ---------------------------------------------------------------------------
+// Open-system dynamics (Sec. III.A): the Lindblad master equation, evolved
+// step by step with the midpoint pulses of Sec. III by a Krylov exponential of
+// the Liouvillian on vec(rho). The Liouvillian is not Hermitian, so the
+// Krylov process is Arnoldi (classical Gram-Schmidt, twice) in place of
+// Lanczos' three-term recurrence. The acceptance test is the same a-posteriori
+// estimate: h_{m+1,m} |[exp(tau H_m) e_1]_{m-1}| <= p, with a step split by
+// halving when m_max is reached.
+// ---------------------------------------------------------------------------
+namespace {
+
+using cplx = std::complex<double>;
+
+// exp(t A) e_1 for a small complex m x m matrix (row-major): scaling and
+// squaring of a truncated Taylor series (Moler and Van Loan, "Nineteen
+// dubious ways to compute the exponential of a matrix", method 3), with the
+// scaled norm at most 1/2 so the series stops below 1e-18 relative.
+std::vector<cplx> small_expm_e1(const std::vector<cplx>& A, int lda, int m, double t) {
+  double nrm = 0.0;
+  for (int j = 0; j < m; ++j) {
+    double col = 0.0;
+    for (int i = 0; i < m; ++i) col += std::abs(A[(size_t)i * lda + j]);
+    nrm = std::max(nrm, col);
+  }
+  nrm *= std::fabs(t);
+  int sq = 0;
+  while (nrm > 0.5 && sq < 200) {
+    nrm *= 0.5;
+    ++sq;
+  }
+  const double scale = std::ldexp(t, -sq);
+  std::vector<cplx> X((size_t)m * m), R((size_t)m * m, 0.0), term((size_t)m * m, 0.0), tmp((size_t)m * m);
+  for (int i = 0; i < m; ++i)
+    for (int j = 0; j < m; ++j) X[(size_t)i * m + j] = scale * A[(size_t)i * lda + j];
+  for (int i = 0; i < m; ++i) R[(size_t)i * m + i] = term[(size_t)i * m + i] = 1.0;
+  auto matmul = [&](const std::vector<cplx>& a, const std::vector<cplx>& b, std::vector<cplx>& c) {
+    for (int i = 0; i < m; ++i)
+      for (int j = 0; j < m; ++j) {
+        cplx acc = 0.0;
+        for (int k = 0; k < m; ++k) acc += a[(size_t)i * m + k] * b[(size_t)k * m + j];
+        c[(size_t)i * m + j] = acc;
+      }
+  };
+  for (int k = 1; k <= 40; ++k) {
+    matmul(term, X, tmp);
+    double tn = 0.0, rn = 0.0;
+    for (size_t e = 0; e < tmp.size(); ++e) {
+      term[e] = tmp[e] / (double)k;
+      R[e] += term[e];
+      tn = std::max(tn, std::abs(term[e]));
+      rn = std::max(rn, std::abs(R[e]));
+    }
+    if (tn <= 1e-18 * rn) break;
+  }
+  for (int s = 0; s < sq; ++s) {
+    matmul(R, R, tmp);
+    R.swap(tmp);
+  }
+  std::vector<cplx> u(m);
+  for (int i = 0; i < m; ++i) u[i] = R[(size_t)i * m];
+  return u;
+}
+
+}  // namespace
+
+extern "C" rsv_status rsv_lindblad_run(rsv_ctx* ctx, const rsv_problem* problem, const rsv_config* config,
+                                       const double* g_dephasing, const double* g_relaxation, const void* rho0,
+                                       void* rho_out, double* occ_out, int32_t capacity_rows, int32_t* n_rows,
+                                       rsv_stats* stats_out) {
+  g_last_error.clear();
+  if (!ctx || !config || !n_rows) return fail(RSV_ERR_INVALID_ARG, "NULL argument");
+  RSV_TRY(validate_problem(problem));
+  const int n = problem->n_atoms, T = problem->t_ns;
+  if (n > kLindbladMaxAtoms)
+    return fail(RSV_ERR_INVALID_ARG, "Lindblad evolution holds 4^n_atoms amplitudes: n_atoms must be <= " +
+                                         std::to_string(kLindbladMaxAtoms));
+  if (problem->initial_state)
+    return fail(RSV_ERR_INVALID_ARG, "pass the initial density matrix as rho0 (problem->initial_state must be NULL)");
+  rsv_config cfg = *config;
+  if (cfg.dt_ns < 1) return fail(RSV_ERR_INVALID_ARG, "dt_ns must be >= 1");
+  if (cfg.precision != RSV_C128) return fail(RSV_ERR_INVALID_ARG, "Lindblad evolution runs in complex128 only");
+  if (cfg.m_max == 0) cfg.m_max = 30;
+  if (cfg.m_max < 2 || cfg.m_max > kLindbladMaxKrylov)
+    return fail(RSV_ERR_INVALID_ARG, "m_max must be in [2, " + std::to_string(kLindbladMaxKrylov) + "]");
+  if (cfg.krylov_tol <= 0.0) cfg.krylov_tol = 1e-12;
+  if (cfg.max_substeps <= 0) cfg.max_substeps = 64;
+  if (cfg.obs_stride < 0) return fail(RSV_ERR_INVALID_ARG, "obs_stride must be >= 0");
+  for (int i = 0; i < n; ++i) {
+    const double a = g_dephasing ? g_dephasing[i] : 0.0, b = g_relaxation ? g_relaxation[i] : 0.0;
+    if (!(a >= 0.0 && b >= 0.0 && std::isfinite(a) && std::isfinite(b)))
+      return fail(RSV_ERR_INVALID_ARG, "noise rates must be finite and >= 0");
+  }
+  const int K = num_steps(T, cfg.dt_ns);
+  const int stride = cfg.obs_stride;
+  const int rows = 1 + (stride > 0 ? K / stride : 0) + ((stride == 0 || K % stride != 0) ? 1 : 0);
+  *n_rows = rows;
+  if (!occ_out && !rho_out) return RSV_OK;
+  std::vector<double> v_atoms;
+  RSV_TRY(pair_energies(n, problem->dim, problem->positions_um, problem->c6, v_atoms));
+  std::vector<StepParams> sp;
+  RSV_TRY(step_params(problem, cfg.dt_ns, sp));
+
+  struct Held {
+    rsv_ctx* ctx;
+    std::vector<void*> bufs;
+    ~Held() {
+      if (!bufs.empty()) cudaStreamSynchronize(ctx->stream);
+      for (void* p : bufs) ctx->arena.release(p);
+    }
+  } held{ctx, {}};
+  auto alloc = [&](size_t bytes, void** p) -> rsv_status {
+    RSV_TRY(ctx->arena.alloc(bytes, p));
+    held.bufs.push_back(*p);
+    return RSV_OK;
+  };
+  const int64_t dim = int64_t(1) << n, total = dim * dim;
+  const size_t vbytes = (size_t)total * 16;
+  const int m_max = cfg.m_max;
+  void *rho = nullptr, *w = nullptr;
+  std::vector<void*> basis(m_max, nullptr);
+  RSV_TRY(alloc(vbytes, &rho));
+  RSV_TRY(alloc(vbytes, &w));
+  for (int k = 0; k < m_max; ++k) RSV_TRY(alloc(vbytes, &basis[k]));
+  // device pointer slots: basis 0 .. m_max - 1, then rho, then w
+  void** d_ptrs = nullptr;
+  double *d_E = nullptr, *d_coef = nullptr, *d_dots = nullptr, *d_norm = nullptr, *d_part = nullptr;
+  const int grid = 4 * ctx->num_sms;
+  RSV_TRY(alloc(sizeof(void*) * (m_max + 2), (void**)&d_ptrs));
+  RSV_TRY(alloc(sizeof(double) * dim, (void**)&d_E));
+  RSV_TRY(alloc(sizeof(double) * 2 * m_max, (void**)&d_coef));
+  RSV_TRY(alloc(sizeof(double) * 2 * m_max, (void**)&d_dots));
+  RSV_TRY(alloc(sizeof(double), (void**)&d_norm));
+  RSV_TRY(alloc(sizeof(double) * std::max<size_t>((size_t)grid * 2 * m_max, (size_t)grid), (void**)&d_part));
+
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  cudaSetDevice(ctx->device);
+  cudaStream_t st = ctx->stream;
+  const auto t0 = std::chrono::steady_clock::now();
+  rsv_stats stats{};
+  stats.krylov_dim_max = m_max;
+  std::vector<void*> ptrs(basis);
+  ptrs.push_back(rho);
+  ptrs.push_back(w);
+  void** const rho_slot = d_ptrs + m_max;
+  void** const w_slot = d_ptrs + m_max + 1;
+  RSV_CUDA(cudaMemcpyAsync(d_ptrs, ptrs.data(), sizeof(void*) * ptrs.size(), cudaMemcpyHostToDevice, st));
+  if (rho0) {
+    RSV_CUDA(cudaMemcpyAsync(rho, rho0, vbytes, cudaMemcpyHostToDevice, st));
+  } else {
+    RSV_CUDA(cudaMemsetAsync(rho, 0, vbytes, st));
+    const double one[2] = {1.0, 0.0};
+    RSV_CUDA(cudaMemcpyAsync(rho, one, sizeof(one), cudaMemcpyHostToDevice, st));
+  }
+  int64_t launches = 0;
+  auto nchunks_for = [&](int nvec) {
+    return (int)std::max<int64_t>(1, std::min<int64_t>((total + kThreads - 1) / kThreads, (grid + nvec - 1) / nvec));
+  };
+  // <V_k, x> for k < nvec (slots from `first`), to the host
+  std::vector<double> dots(2 * m_max);
+  auto multi_dot = [&](void** first, int nvec, const void* x) -> rsv_status {
+    RSV_CUDA(launch_multi_dot((const void* const*)first, nvec, x, total, nchunks_for(nvec), d_part, d_dots, st));
+    launches += 2;
+    RSV_CUDA(cudaMemcpyAsync(dots.data(), d_dots, sizeof(double) * 2 * nvec, cudaMemcpyDeviceToHost, st));
+    RSV_CUDA(cudaStreamSynchronize(st));
+    return RSV_OK;
+  };
+  // y = (overwrite ? 0 : y) - sum_k c_k V_k; returns |y|^2
+  auto multi_axpy = [&](void** first, const std::vector<double>& c, int nvec, void* y, bool overwrite,
+                        double* norm2) -> rsv_status {
+    RSV_CUDA(cudaMemcpyAsync(d_coef, c.data(), sizeof(double) * 2 * nvec, cudaMemcpyHostToDevice, st));
+    RSV_CUDA(launch_multi_axpy((const void* const*)first, d_coef, nvec, y, total, overwrite, grid, d_part, d_norm,
+                               st));
+    launches += 2;
+    if (norm2) {
+      RSV_CUDA(cudaMemcpyAsync(norm2, d_norm, sizeof(double), cudaMemcpyDeviceToHost, st));
+      RSV_CUDA(cudaStreamSynchronize(st));
+    }
+    return RSV_OK;
+  };
+  // occupation rows: tr(rho n_i) from the diagonal
+  std::vector<double> diag(2 * dim);
+  int row = 0;
+  auto record = [&]() -> rsv_status {
+    if (row < capacity_rows && occ_out) {
+      RSV_CUDA(cudaMemcpy2DAsync(diag.data(), 16, rho, (size_t)(dim + 1) * 16, 16, (size_t)dim,
+                                 cudaMemcpyDeviceToHost, st));
+      RSV_CUDA(cudaStreamSynchronize(st));
+      for (int i = 0; i < n; ++i) {
+        const int q = n - 1 - i;
+        double s = 0.0;
+        for (int64_t r = 0; r < dim; ++r)
+          if ((r >> q) & 1) s += diag[2 * r];
+        occ_out[(size_t)row * n + i] = s;
+      }
+    }
+    ++row;
+    return RSV_OK;
+  };
+  RSV_TRY(record());
+
+  // bit-order pair energies and rates
+  std::vector<double> vb((size_t)n * n), E(dim);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) vb[(size_t)(n - 1 - i) * n + (n - 1 - j)] = v_atoms[(size_t)i * n + j];
+  LindbladParams lp{};
+  lp.n = n;
+  for (int i = 0; i < n; ++i) {
+    lp.gd[n - 1 - i] = g_dephasing ? g_dephasing[i] : 0.0;
+    lp.gr[n - 1 - i] = g_relaxation ? g_relaxation[i] : 0.0;
+  }
+  std::vector<cplx> H((size_t)(m_max + 1) * m_max);
+  for (int k = 0; k < K; ++k) {
+    // E(b) = E(b without its lowest bit q) - delta_q + sum_{p in the rest} V_qp
+    E[0] = 0.0;
+    for (int64_t b = 1; b < dim; ++b) {
+      const int q = __builtin_ctzll((unsigned long long)b);
+      const int64_t rest = b & (b - 1);
+      double e = E[rest] - sp[k].delta[q];
+      for (int64_t r2 = rest; r2; r2 &= r2 - 1) e += vb[(size_t)q * n + __builtin_ctzll((unsigned long long)r2)];
+      E[b] = e;
+    }
+    RSV_CUDA(cudaMemcpyAsync(d_E, E.data(), sizeof(double) * dim, cudaMemcpyHostToDevice, st));
+    for (int q = 0; q < n; ++q) {
+      lp.hre[q] = sp[k].half_omega[q] * std::cos(sp[k].phi[q]);
+      lp.him[q] = sp[k].half_omega[q] * std::sin(sp[k].phi[q]);
+    }
+    double tau_rem = sp[k].tau;
+    int restarts = 0;
+    while (tau_rem > 0.0) {
+      RSV_TRY(multi_dot(rho_slot, 1, rho));
+      const double beta0 = std::sqrt(std::max(0.0, dots[0]));
+      if (!(beta0 > 0.0)) break;  // rho = 0 stays 0
+      RSV_TRY(multi_axpy(rho_slot, {-1.0 / beta0, 0.0}, 1, basis[0], true, nullptr));
+      std::fill(H.begin(), H.end(), cplx(0.0));
+      int m = 0;
+      double tau_taken = 0.0, err = 0.0;
+      std::vector<cplx> u;
+      for (int j = 0; j < m_max; ++j) {
+        RSV_CUDA(launch_lindblad_apply(basis[j], w, d_E, lp, grid, st));
+        launches += 1;
+        std::vector<double> c(2 * (j + 1));
+        double norm2 = 0.0;
+        for (int pass = 0; pass < 2; ++pass) {
+          RSV_TRY(multi_dot(d_ptrs, j + 1, w));
+          for (int i = 0; i <= j; ++i) {
+            H[(size_t)i * m_max + j] += cplx(dots[2 * i], dots[2 * i + 1]);
+            c[2 * i] = dots[2 * i];
+            c[2 * i + 1] = dots[2 * i + 1];
+          }
+          RSV_TRY(multi_axpy(d_ptrs, c, j + 1, w, false, pass == 1 ? &norm2 : nullptr));
+        }
+        const double hn = std::sqrt(std::max(0.0, norm2));
+        H[(size_t)(j + 1) * m_max + j] = hn;
+        double hmax = 0.0;
+        for (int i = 0; i <= j + 1; ++i)
+          for (int l = 0; l <= j; ++l) hmax = std::max(hmax, std::abs(H[(size_t)i * m_max + l]));
+        u = small_expm_e1(H, m_max, j + 1, tau_rem);
+        err = hn * std::abs(u[j]);
+        if (hn <= 1e-13 * std::max(1.0, hmax) || err <= cfg.krylov_tol) {
+          m = j + 1;
+          tau_taken = tau_rem;
+          break;
+        }
+        if (j == m_max - 1) {
+          double t = tau_rem;
+          for (int h = 0; h < 200 && err > cfg.krylov_tol; ++h) {
+            t *= 0.5;
+            u = small_expm_e1(H, m_max, j + 1, t);
+            err = hn * std::abs(u[j]);
+          }
+          if (err > cfg.krylov_tol)
+            return fail(RSV_ERR_NOT_CONVERGED, "Arnoldi space did not reach the tolerance (non-finite values?)");
+          m = j + 1;
+          tau_taken = t;
+          break;
+        }
+        RSV_TRY(multi_axpy(w_slot, {-1.0 / hn, 0.0}, 1, basis[j + 1], true, nullptr));
+      }
+      std::vector<double> c(2 * m);
+      for (int i = 0; i < m; ++i) {
+        c[2 * i] = -beta0 * u[i].real();
+        c[2 * i + 1] = -beta0 * u[i].imag();
+      }
+      RSV_TRY(multi_axpy(d_ptrs, c, m, rho, true, nullptr));
+      stats.krylov_iterations += m;
+      stats.max_error_estimate = std::max(stats.max_error_estimate, err);
+      tau_rem -= tau_taken;
+      if (tau_rem <= 1e-15 * sp[k].tau) break;
+      if (++restarts > cfg.max_substeps)
+        return fail(RSV_ERR_NOT_CONVERGED, "step " + std::to_string(k) + " needed more than max_substeps restarts");
+      stats.substeps += 1;
+    }
+    stats.steps += 1;
+    if ((stride > 0 && (k + 1) % stride == 0) || k + 1 == K) RSV_TRY(record());
+  }
+  if (rho_out) RSV_CUDA(cudaMemcpyAsync(rho_out, rho, vbytes, cudaMemcpyDeviceToHost, st));
+  RSV_CUDA(cudaStreamSynchronize(st));
+  stats.kernel_launches = launches;
+  stats.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  stats.tile_passes = 1;
+  *n_rows = row;
+  if (stats_out) *stats_out = stats;
+  return RSV_OK;
+}
+
+// ---------------------------------------------------------------------------
 // Serving: requests are admitted by device-memory footprint; each admitted
 // solve runs on a worker thread with its own CUDA stream, so solves of
 // different requests overlap on the device.
