@@ -585,6 +585,14 @@ def profile_batch():
     return 0
 
 
+def profile_legs():
+    """The Lindblad and gradient legs alone, once each (ncu launch lists)."""
+    from paper_2510_09813_b300 import api
+    from paper_2510_09813_b300 import workloads as W
+    print(json.dumps({"lindblad": lindblad_leg(api, W, 0), "gradient": gradient_leg(api, W, 0)}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -603,9 +611,12 @@ def main():
     ap.add_argument("--profile-case", type=int, default=0, metavar="N",
                     help="run the small ncu case at N atoms instead of the benchmark")
     ap.add_argument("--profile-batch", action="store_true", help="run the small batched ncu case")
+    ap.add_argument("--profile-legs", action="store_true", help="run only the Lindblad and gradient legs")
     args = ap.parse_args()
     if args.profile_batch:
         return profile_batch()
+    if args.profile_legs:
+        return profile_legs()
     if args.profile_case:
         return profile_case(args.profile_case)
     if args.warmup < 3:
