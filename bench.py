@@ -327,7 +327,8 @@ def gradient_leg(api, W, device: int):
 
 
 LINDBLAD_WORKLOAD = ("10-atom chain at 6 um, Omega = 2*pi rad/us, delta = 0, Rydberg dephasing 0.2/us and decay "
-                     "0.1/us on every atom, first 300 ns, dt = 10 ns; rho of 4^10 complex128 amplitudes")
+                     "0.1/us on every atom, first 300 ns, dt = 10 ns; rho of 4^10 amplitudes, complex128 and "
+                     "complex64 (FP32 products, FP64-class reductions)")
 
 
 def lindblad_leg(api, W, device: int):
@@ -336,16 +337,21 @@ def lindblad_leg(api, W, device: int):
     ctx = api.Context(device)
     g_d, g_r = np.full(10, 0.2), np.full(10, 0.1)
     api.lindblad_run(ctx, W.rabi_chain(n=10, t_ns=20), 10, g_d, g_r, obs_stride=0)  # warm-up
-    t0 = time.perf_counter()
-    res = api.lindblad_run(ctx, prob, 10, g_d, g_r, obs_stride=0)
-    sec = time.perf_counter() - t0
+    api.lindblad_run(ctx, W.rabi_chain(n=10, t_ns=20), 10, g_d, g_r, obs_stride=0, precision="c64")
+    out = {"workload": LINDBLAD_WORKLOAD}
+    for prec in ("c128", "c64"):
+        t0 = time.perf_counter()
+        res = api.lindblad_run(ctx, prob, 10, g_d, g_r, obs_stride=0, precision=prec)
+        sec = time.perf_counter() - t0
+        st = res.stats
+        out[prec] = {"seconds": sec, "steps_per_s": st["steps"] / sec,
+                     "krylov_iterations_per_step": st["krylov_iterations"] / st["steps"],
+                     "krylov_iterations_per_s": st["krylov_iterations"] / sec, "substeps": st["substeps"],
+                     "kernel_launches": st["kernel_launches"],
+                     "trace": float(np.trace(res.rho.astype(np.complex128)).real),
+                     "rydberg_population": float(res.occupations[-1].sum())}
     ctx.close()
-    st = res.stats
-    return {"workload": LINDBLAD_WORKLOAD, "seconds": sec, "steps_per_s": st["steps"] / sec,
-            "krylov_iterations_per_step": st["krylov_iterations"] / st["steps"],
-            "krylov_iterations_per_s": st["krylov_iterations"] / sec, "substeps": st["substeps"],
-            "kernel_launches": st["kernel_launches"], "trace": float(np.trace(res.rho).real),
-            "rydberg_population": float(res.occupations[-1].sum())}
+    return out
 
 
 # ---------------------------------------------------------------------------

@@ -414,21 +414,23 @@ RSV_API rsv_status rsv_gradient(rsv_ctx* ctx, const rsv_problem* problem, const 
  * n_i and spontaneous decay L = sqrt(g_relaxation[i]) |0><1|_i, rates in 1/us
  * (either array may be NULL = all zero).
  *
- * rho is a 2^n x 2^n complex128 matrix, row-major (basis order as for states),
- * held on the device as a vector of 4^n amplitudes; n_atoms <= 14. Each step is
- * a Krylov exponential of the Liouvillian: Arnoldi (the Liouvillian is not
+ * rho is a 2^n x 2^n matrix, row-major (basis order as for states), held on
+ * the device as a vector of 4^n amplitudes in config->precision; n_atoms <= 14.
+ * RSV_C128 computes in FP64; RSV_C64 keeps rho and the Krylov basis in FP32
+ * with FP32 products and FP64-class inner products and norms. Each step is a
+ * Krylov exponential of the Liouvillian: Arnoldi (the Liouvillian is not
  * Hermitian) with classical Gram-Schmidt twice, accepted when
- * h_{m+1,m} |[exp(tau H_m) e_1]_{m-1}| <= krylov_tol (default 1e-12), and a
- * step split by halving when m_max (default 30, at most 64) is reached.
- * config->precision must be RSV_C128; problem->initial_state must be NULL.
+ * h_{m+1,m} |[exp(tau H_m) e_1]_{m-1}| <= krylov_tol (default 1e-12 for
+ * RSV_C128, 1e-7 for RSV_C64), and a step split by halving when m_max
+ * (default 30, at most 64) is reached. problem->initial_state must be NULL.
  *
- * rho0: host [2^n][2^n] complex128 initial density matrix, or NULL for
- * |0...0><0...0|. rho_out (nullable): host [2^n][2^n] complex128, the final
- * rho. occ_out (nullable): host [rows][n_atoms] of tr(rho n_i) at t = 0,
+ * rho0: host [2^n][2^n] initial density matrix in config->precision, or NULL
+ * for |0...0><0...0|. rho_out (nullable): host [2^n][2^n] in
+ * config->precision, the final rho. occ_out (nullable): host [rows][n_atoms] of tr(rho n_i) at t = 0,
  * after every obs_stride-th step and at the end; at most capacity_rows rows
  * are written and *n_rows receives the count. With rho_out and occ_out both
  * NULL, only *n_rows is set. Device memory from the context arena:
- * (m_max + 2) vectors of 16 * 4^n bytes. Synchronises the context stream. */
+ * (m_max + 2) vectors of 4^n amplitudes (16 or 8 bytes each). Synchronises the context stream. */
 RSV_API rsv_status rsv_lindblad_run(rsv_ctx* ctx, const rsv_problem* problem, const rsv_config* config,
                                     const double* g_dephasing, const double* g_relaxation, const void* rho0,
                                     void* rho_out, double* occ_out, int32_t capacity_rows, int32_t* n_rows,

@@ -531,12 +531,13 @@ class LindbladResult:
 
 
 def lindblad_run(ctx: Context, problem, dt_ns: int, g_dephasing=None, g_relaxation=None, rho0=None,
-                 krylov_tol=0.0, m_max=0, max_substeps=0, obs_stride=1) -> LindbladResult:
+                 krylov_tol=0.0, m_max=0, max_substeps=0, obs_stride=1, precision="c128") -> LindbladResult:
     """rsv_lindblad_run: the Lindblad master equation with per-atom Rydberg
-    dephasing and spontaneous decay rates (1/us), complex128."""
+    dephasing and spontaneous decay rates (1/us)."""
     pa = L.ProblemArgs.from_problem(problem)
     n = pa.n
-    cfg = L.make_config(dt_ns, "c128", krylov_tol, m_max, max_substeps, obs_stride)
+    cfg = L.make_config(dt_ns, precision, krylov_tol, m_max, max_substeps, obs_stride)
+    cdt = amp_dtype(precision)
 
     def rates(g):
         if g is None:
@@ -549,7 +550,7 @@ def lindblad_run(ctx: Context, problem, dt_ns: int, g_dephasing=None, g_relaxati
     gd, gr = rates(g_dephasing), rates(g_relaxation)
     r0 = None
     if rho0 is not None:
-        r0 = np.ascontiguousarray(np.asarray(rho0, dtype=np.complex128))
+        r0 = np.ascontiguousarray(np.asarray(rho0, dtype=cdt))
         if r0.shape != (2 ** n, 2 ** n):
             raise ValueError("rho0 must be [2^n][2^n]")
     nulld = C.POINTER(C.c_double)()
@@ -557,7 +558,7 @@ def lindblad_run(ctx: Context, problem, dt_ns: int, g_dephasing=None, g_relaxati
     args = (ctx.handle, C.byref(pa.struct), C.byref(cfg), L._dptr(gd) if gd is not None else nulld,
             L._dptr(gr) if gr is not None else nulld, None if r0 is None else r0.ctypes.data)
     check(L.lib().rsv_lindblad_run(*args, None, nulld, 0, C.byref(rows), None))
-    rho = np.empty((2 ** n, 2 ** n), dtype=np.complex128)
+    rho = np.empty((2 ** n, 2 ** n), dtype=cdt)
     occ = np.empty((rows.value, n))
     st = L.Stats_()
     check(L.lib().rsv_lindblad_run(*args, rho.ctypes.data, L._dptr(occ), rows.value, C.byref(rows), C.byref(st)))

@@ -174,8 +174,9 @@ cudaError_t launch_generator(const void* mu, const void* nu, int64_t dim, bool c
 cudaError_t launch_overlap(const void* a, const void* b, int64_t dim, bool c64, double* partials, int grid,
                            cudaStream_t stream);
 
-// Lindblad master equation on vec(rho), complex128 (lindblad_kernels.cu).
-constexpr int kLindbladMaxAtoms = 14;   // vec(rho) of 4^14 amplitudes (4 GiB)
+// Lindblad master equation on vec(rho) (lindblad_kernels.cu), complex128 or
+// complex64 (FP32 products, FP64-class reductions).
+constexpr int kLindbladMaxAtoms = 14;   // vec(rho) of 4^14 amplitudes
 constexpr int kLindbladMaxKrylov = 64;  // Arnoldi basis vectors
 struct LindbladParams {
   int n;
@@ -183,16 +184,17 @@ struct LindbladParams {
   double hre[kLindbladMaxAtoms], him[kLindbladMaxAtoms];
   double gd[kLindbladMaxAtoms], gr[kLindbladMaxAtoms];
 };
-// y = L(x); E: [2^n] diagonal energies by bit-order index.
-cudaError_t launch_lindblad_apply(const void* x, void* y, const double* E, const LindbladParams& p, int grid,
+// y = L(x); E: [2^n] diagonal energies by bit-order index, in the working
+// precision (float for c64, double for c128).
+cudaError_t launch_lindblad_apply(const void* x, void* y, const void* E, const LindbladParams& p, bool c64, int grid,
                                   cudaStream_t stream);
 // out[2k], out[2k+1] = Re, Im <V_k, w> for k < nvec (device array of nvec
 // device pointers); partials needs nchunks * nvec * 2 doubles.
-cudaError_t launch_multi_dot(const void* const* V, int nvec, const void* w, int64_t total, int nchunks,
+cudaError_t launch_multi_dot(const void* const* V, int nvec, const void* w, int64_t total, bool c64, int nchunks,
                              double* partials, double* out, cudaStream_t stream);
 // w = (overwrite ? 0 : w) - sum_k (coef[2k] + i coef[2k+1]) V_k; *norm2_out = |w|^2
 // (device); partials needs grid doubles.
-cudaError_t launch_multi_axpy(const void* const* V, const double* coef, int nvec, void* w, int64_t total,
+cudaError_t launch_multi_axpy(const void* const* V, const double* coef, int nvec, void* w, int64_t total, bool c64,
                               bool overwrite, int grid, double* partials, double* norm2_out, cudaStream_t stream);
 
 // Sampling (sample_kernels.cu)

@@ -2408,11 +2408,12 @@ extern "C" rsv_status rsv_lindblad_run(rsv_ctx* ctx, const rsv_problem* problem,
     return fail(RSV_ERR_INVALID_ARG, "pass the initial density matrix as rho0 (problem->initial_state must be NULL)");
   rsv_config cfg = *config;
   if (cfg.dt_ns < 1) return fail(RSV_ERR_INVALID_ARG, "dt_ns must be >= 1");
-  if (cfg.precision != RSV_C128) return fail(RSV_ERR_INVALID_ARG, "Lindblad evolution runs in complex128 only");
+  if (cfg.precision != RSV_C128 && cfg.precision != RSV_C64) return fail(RSV_ERR_INVALID_ARG, "bad precision");
+  const bool c64 = cfg.precision == RSV_C64;
   if (cfg.m_max == 0) cfg.m_max = 30;
   if (cfg.m_max < 2 || cfg.m_max > kLindbladMaxKrylov)
     return fail(RSV_ERR_INVALID_ARG, "m_max must be in [2, " + std::to_string(kLindbladMaxKrylov) + "]");
-  if (cfg.krylov_tol <= 0.0) cfg.krylov_tol = 1e-12;
+  if (cfg.krylov_tol <= 0.0) cfg.krylov_tol = c64 ? 1e-7 : 1e-12;
   if (cfg.max_substeps <= 0) cfg.max_substeps = 64;
   if (cfg.obs_stride < 0) return fail(RSV_ERR_INVALID_ARG, "obs_stride must be >= 0");
   for (int i = 0; i < n; ++i) {
@@ -2444,7 +2445,8 @@ extern "C" rsv_status rsv_lindblad_run(rsv_ctx* ctx, const rsv_problem* problem,
     return RSV_OK;
   };
   const int64_t dim = int64_t(1) << n, total = dim * dim;
-  const size_t vbytes = (size_t)total * 16;
+  const size_t abytes = c64 ? 8 : 16;  // bytes per amplitude
+  const size_t vbytes = (size_t)total * abytes;
   const int m_max = cfg.m_max;
   void *rho = nullptr, *w = nullptr;
   std::vector<void*> basis(m_max, nullptr);
@@ -2453,10 +2455,11 @@ extern "C" rsv_status rsv_lindblad_run(rsv_ctx* ctx, const rsv_problem* problem,
   for (int k = 0; k < m_max; ++k) RSV_TRY(alloc(vbytes, &basis[k]));
   // device pointer slots: basis 0 .. m_max - 1, then rho, then w
   void** d_ptrs = nullptr;
-  double *d_E = nullptr, *d_coef = nullptr, *d_dots = nullptr, *d_norm = nullptr, *d_part = nullptr;
+  void* d_E = nullptr;
+  double *d_coef = nullptr, *d_dots = nullptr, *d_norm = nullptr, *d_part = nullptr;
   const int grid = 4 * ctx->num_sms;
   RSV_TRY(alloc(sizeof(void*) * (m_max + 2), (void**)&d_ptrs));
-  RSV_TRY(alloc(sizeof(double) * dim, (void**)&d_E));
+  RSV_TRY(alloc(sizeof(double) * dim, &d_E));
   RSV_TRY(alloc(sizeof(double) * 2 * m_max, (void**)&d_coef));
   RSV_TRY(alloc(sizeof(double) * 2 * m_max, (void**)&d_dots));
   RSV_TRY(alloc(sizeof(double), (void**)&d_norm));
@@ -2478,8 +2481,9 @@ extern "C" rsv_status rsv_lindblad_run(rsv_ctx* ctx, const rsv_problem* problem,
     RSV_CUDA(cudaMemcpyAsync(rho, rho0, vbytes, cudaMemcpyHostToDevice, st));
   } else {
     RSV_CUDA(cudaMemsetAsync(rho, 0, vbytes, st));
-    const double one[2] = {1.0, 0.0};
-    RSV_CUDA(cudaMemcpyAsync(rho, one, sizeof(one), cudaMemcpyHostToDevice, st));
+    const double one_d[2] = {1.0, 0.0};
+    const float one_f[2] = {1.f, 0.f};
+    RSV_CUDA(cudaMemcpyAsync(rho, c64 ? (const void*)one_f : (const void*)one_d, abytes, cudaMemcpyHostToDevice, st));
   }
   int64_t launches = 0;
   auto nchunks_for = [&](int nvec) {
@@ -2488,7 +2492,7 @@ extern "C" rsv_status rsv_lindblad_run(rsv_ctx* ctx, const rsv_problem* problem,
   // <V_k, x> for k < nvec (slots from `first`), to the host
   std::vector<double> dots(2 * m_max);
   auto multi_dot = [&](void** first, int nvec, const void* x) -> rsv_status {
-    RSV_CUDA(launch_multi_dot((const void* const*)first, nvec, x, total, nchunks_for(nvec), d_part, d_dots, st));
+    RSV_CUDA(launch_multi_dot((const void* const*)first, nvec, x, total, c64, nchunks_for(nvec), d_part, d_dots, st));
     launches += 2;
     RSV_CUDA(cudaMemcpyAsync(dots.data(), d_dots, sizeof(double) * 2 * nvec, cudaMemcpyDeviceToHost, st));
     RSV_CUDA(cudaStreamSynchronize(st));
@@ -2498,8 +2502,8 @@ extern "C" rsv_status rsv_lindblad_run(rsv_ctx* ctx, const rsv_problem* problem,
   auto multi_axpy = [&](void** first, const std::vector<double>& c, int nvec, void* y, bool overwrite,
                         double* norm2) -> rsv_status {
     RSV_CUDA(cudaMemcpyAsync(d_coef, c.data(), sizeof(double) * 2 * nvec, cudaMemcpyHostToDevice, st));
-    RSV_CUDA(launch_multi_axpy((const void* const*)first, d_coef, nvec, y, total, overwrite, grid, d_part, d_norm,
-                               st));
+    RSV_CUDA(launch_multi_axpy((const void* const*)first, d_coef, nvec, y, total, c64, overwrite, grid, d_part,
+                               d_norm, st));
     launches += 2;
     if (norm2) {
       RSV_CUDA(cudaMemcpyAsync(norm2, d_norm, sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -2508,18 +2512,19 @@ extern "C" rsv_status rsv_lindblad_run(rsv_ctx* ctx, const rsv_problem* problem,
     return RSV_OK;
   };
   // occupation rows: tr(rho n_i) from the diagonal
-  std::vector<double> diag(2 * dim);
+  std::vector<double> diag(2 * dim);  // the diagonal's amplitudes, as bytes of the working precision
   int row = 0;
   auto record = [&]() -> rsv_status {
     if (row < capacity_rows && occ_out) {
-      RSV_CUDA(cudaMemcpy2DAsync(diag.data(), 16, rho, (size_t)(dim + 1) * 16, 16, (size_t)dim,
+      RSV_CUDA(cudaMemcpy2DAsync(diag.data(), abytes, rho, (size_t)(dim + 1) * abytes, abytes, (size_t)dim,
                                  cudaMemcpyDeviceToHost, st));
       RSV_CUDA(cudaStreamSynchronize(st));
+      const float* df = reinterpret_cast<const float*>(diag.data());
       for (int i = 0; i < n; ++i) {
         const int q = n - 1 - i;
         double s = 0.0;
         for (int64_t r = 0; r < dim; ++r)
-          if ((r >> q) & 1) s += diag[2 * r];
+          if ((r >> q) & 1) s += c64 ? (double)df[2 * r] : diag[2 * r];
         occ_out[(size_t)row * n + i] = s;
       }
     }
@@ -2530,6 +2535,7 @@ extern "C" rsv_status rsv_lindblad_run(rsv_ctx* ctx, const rsv_problem* problem,
 
   // bit-order pair energies and rates
   std::vector<double> vb((size_t)n * n), E(dim);
+  std::vector<float> Ef(c64 ? dim : 0);
   for (int i = 0; i < n; ++i)
     for (int j = 0; j < n; ++j) vb[(size_t)(n - 1 - i) * n + (n - 1 - j)] = v_atoms[(size_t)i * n + j];
   LindbladParams lp{};
@@ -2549,7 +2555,12 @@ extern "C" rsv_status rsv_lindblad_run(rsv_ctx* ctx, const rsv_problem* problem,
       for (int64_t r2 = rest; r2; r2 &= r2 - 1) e += vb[(size_t)q * n + __builtin_ctzll((unsigned long long)r2)];
       E[b] = e;
     }
-    RSV_CUDA(cudaMemcpyAsync(d_E, E.data(), sizeof(double) * dim, cudaMemcpyHostToDevice, st));
+    if (c64) {
+      for (int64_t b = 0; b < dim; ++b) Ef[b] = (float)E[b];
+      RSV_CUDA(cudaMemcpyAsync(d_E, Ef.data(), sizeof(float) * dim, cudaMemcpyHostToDevice, st));
+    } else {
+      RSV_CUDA(cudaMemcpyAsync(d_E, E.data(), sizeof(double) * dim, cudaMemcpyHostToDevice, st));
+    }
     for (int q = 0; q < n; ++q) {
       lp.hre[q] = sp[k].half_omega[q] * std::cos(sp[k].phi[q]);
       lp.him[q] = sp[k].half_omega[q] * std::sin(sp[k].phi[q]);
@@ -2566,7 +2577,7 @@ extern "C" rsv_status rsv_lindblad_run(rsv_ctx* ctx, const rsv_problem* problem,
       double tau_taken = 0.0, err = 0.0;
       std::vector<cplx> u;
       for (int j = 0; j < m_max; ++j) {
-        RSV_CUDA(launch_lindblad_apply(basis[j], w, d_E, lp, grid, st));
+        RSV_CUDA(launch_lindblad_apply(basis[j], w, d_E, lp, c64, grid, st));
         launches += 1;
         std::vector<double> c(2 * (j + 1));
         double norm2 = 0.0;

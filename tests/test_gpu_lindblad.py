@@ -2,10 +2,13 @@
 oracle's dense superoperator exponentials, and its invariants at sizes the
 dense oracle does not reach.
 
-Tolerance: each Krylov piece is accepted at an a-posteriori error of
-p = 1e-12 relative to |rho|_F <= 1, and the pieces add up over the steps, so
-rho and the occupation rows must match to 1e-10 for the sequences used here
-(at most 20 steps).
+Tolerance (complex128): each Krylov piece is accepted at an a-posteriori
+error of p = 1e-12 relative to |rho|_F <= 1, and the pieces add up over the
+steps, so rho and the occupation rows must match to 1e-10 for the sequences
+used here (at most 20 steps). complex64: p = 1e-7 per piece plus FP32
+rounding of the diagonal differences E(r) - E(c) (about 2^-24 of up to 1e3
+rad/us, i.e. a phase error near 6e-7 per 10-ns step), so 20 steps stay below
+5e-5.
 """
 import numpy as np
 import pytest
@@ -17,6 +20,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 TOL = 1e-10
+TOL_C64 = 5e-5
 POS = np.array([[0.0, 0.0], [6.0, 0.0], [3.0, 5.5], [9.0, 5.0], [12.0, 0.0], [6.0, 10.0], [0.0, 11.0]])
 
 
@@ -56,6 +60,22 @@ def test_lindblad_matches_oracle(ctx, n, t_ns, dt, orow, drow, prow):
     assert np.max(np.abs(got.rho - rho)) <= TOL
     assert np.max(np.abs(got.occupations - occ)) <= TOL
     assert got.stats["steps"] == len(O.step_schedule(t_ns, dt))
+
+
+@pytest.mark.parametrize("n,t_ns,dt,orow,drow,prow", [(1, 200, 10, 1, 1, 1), (3, 60, 10, 1, 3, 3),
+                                                      (5, 20, 10, 1, 1, 0)])
+def test_lindblad_complex64_matches_oracle(ctx, n, t_ns, dt, orow, drow, prow):
+    rng = np.random.default_rng(600 + n)
+    om = rng.uniform(2, 10, (orow, t_ns))
+    de = rng.normal(0, 5, (drow, t_ns))
+    ph = None if prow == 0 else rng.uniform(-1, 1, (prow, t_ns))
+    gd, gr = rng.uniform(0, 2, n), rng.uniform(0, 2, n)
+    prob = W.Problem(positions=POS[:n].copy(), c6=W.C6_DEFAULT, t_ns=t_ns, omega=om, delta=de, phi=ph)
+    got = api().lindblad_run(ctx, prob, dt, gd, gr, obs_stride=1, precision="c64")
+    rho, occ = O.lindblad_evolve(prob.positions, prob.c6, t_ns, dt, om, de, ph, gd, gr)
+    assert got.rho.dtype == np.complex64
+    assert np.max(np.abs(got.rho.astype(np.complex128) - rho)) <= TOL_C64
+    assert np.max(np.abs(got.occupations - occ)) <= TOL_C64
 
 
 def test_lindblad_from_a_given_mixed_state(ctx):
@@ -110,6 +130,11 @@ def test_lindblad_stays_a_density_matrix_at_n9(ctx):
     assert np.max(np.abs(rho - rho.conj().T)) <= 1e-12
     assert np.min(np.linalg.eigvalsh(0.5 * (rho + rho.conj().T))) >= -1e-10
     assert np.allclose(got.occupations[-1], np.real(np.diag(rho)) @ O.occupation_bits(n), rtol=0, atol=1e-12)
+    g32 = api().lindblad_run(ctx, prob, 10, rng.uniform(0, 1, n), rng.uniform(0, 1, n), obs_stride=0,
+                             precision="c64")
+    r32 = g32.rho.astype(np.complex128)
+    assert abs(np.trace(r32) - 1.0) <= 2e-5
+    assert np.max(np.abs(r32 - r32.conj().T)) <= 1e-5
 
 
 def test_lindblad_rejects_bad_arguments(ctx):
