@@ -58,6 +58,7 @@ constexpr int kTileBitsC128 = kTileBitsD;
 constexpr int kMinSegmentBits = 4;   // contiguous amplitude bits of the strided pass
 constexpr int kMaxSingleGBits = 2;   // bits above the tile resolved in the single pass
 constexpr int kMaxGBits = 12;        // partner bits through L2 a pass can take
+constexpr int kFirstPassGBits = 0;   // two-pass: partner bits the contiguous pass takes (first_pass_gbits)
 
 int64_t amp_bytes(int precision) { return precision == RSV_C64 ? 8 : 16; }
 
@@ -198,6 +199,16 @@ struct Plan {
   int L_a = 0;         // tile bits of the first pass (Q table size)
 };
 
+// L2 partner bits of a two-pass matvec taken by the contiguous first pass
+// (amplitude bits [L, L + g)) instead of the strided second pass, whose L2
+// traffic (8 bytes per amplitude per partner bit) is what bounds it.
+int first_pass_gbits() {
+  const char* e = std::getenv("RSV_FIRST_GBITS");
+  if (!e) return kFirstPassGBits;
+  const int v = std::atoi(e);
+  return (v >= 0 && v <= 4) ? v : kFirstPassGBits;
+}
+
 Plan make_plan(int n, bool c64, int num_sms, int seg_bits = kMinSegmentBits, int f1_fast = 0) {
   Plan p;
   const int lt = c64 ? kTileBitsC64 : kTileBitsC128;
@@ -218,10 +229,11 @@ Plan make_plan(int n, bool c64, int num_sms, int seg_bits = kMinSegmentBits, int
   } else if (n - lt <= kMaxSingleGBits) {
     geom(p.a, lt, lt, lt, n - lt);
   } else {
-    geom(p.a, lt, lt, lt, 0);
-    const int h = std::min(n - lt, lt - seg_bits);
+    const int ga = std::min(first_pass_gbits(), n - lt - 1);
+    geom(p.a, lt, lt, lt, ga);
+    const int h = std::min(n - lt - ga, lt - seg_bits);
     const int c = lt - h;
-    geom(p.b, lt, c, lt, 0);
+    geom(p.b, lt, c, lt + ga, 0);
     p.b.split_h = (lt - c) > 8;
     p.b.f1_fast = std::min(f1_fast, p.b.a - p.b.c);
     p.b.nG = p.b.nF2;  // callers check nG <= kMaxGBits
