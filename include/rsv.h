@@ -362,6 +362,16 @@ RSV_API rsv_status rsv_run_shots(rsv_ctx* ctx, const rsv_problem* problem, const
                                  const double* omega_scale, const double* delta_shift, const double* pos_shift_um,
                                  double* occ_mean, int32_t capacity_rows, int32_t* n_rows);
 
+/* Solves `count` problems with one config and returns one result per
+ * problem in outs[count] (each freed with rsv_result_free). Problems of at
+ * most 20 atoms are evolved together by one batched persistent launch
+ * (rsv_batch_*; their results share it, and it is freed with the last of
+ * them). Larger problems run on the streaming solver one after another, with
+ * m_max < 0 read as the default there. On error every result made so far is
+ * freed and outs[] is NULL. Synchronises the context stream. */
+RSV_API rsv_status rsv_run_batch(rsv_ctx* ctx, const rsv_problem* problems, int32_t count, const rsv_config* config,
+                                 rsv_result** outs);
+
 /* ---- fidelity and gradients ------------------------------------------------ */
 
 /* Overlap of two device states (Sec. III results: fidelity with a target):

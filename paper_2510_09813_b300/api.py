@@ -565,6 +565,18 @@ def lindblad_run(ctx: Context, problem, dt_ns: int, g_dephasing=None, g_relaxati
     return LindbladResult(rho, occ[:rows.value], {k: getattr(st, k) for k, _ in L.Stats_._fields_})
 
 
+def run_batch(ctx: Context, problems, dt_ns: int, precision="c64", krylov_tol=0.0, m_max=0, max_substeps=0,
+              obs_stride=1) -> list:
+    """rsv_run_batch: one Result per problem; registers of at most 20 atoms
+    share one batched launch, larger ones run on the streaming solver."""
+    args = [L.ProblemArgs.from_problem(p) for p in problems]
+    arr = (L.Problem_ * len(args))(*[a.struct for a in args])
+    cfg = L.make_config(dt_ns, precision, krylov_tol, m_max, max_substeps, obs_stride)
+    outs = (C.c_void_p * len(args))()
+    check(L.lib().rsv_run_batch(ctx.handle, arr, len(args), C.byref(cfg), outs))
+    return [Result(ctx, C.c_void_p(outs[i]), args[i].n, precision_code(precision)) for i in range(len(args))]
+
+
 def run(ctx: Context, problem, dt_ns: int, precision="c128", krylov_tol=0.0, m_max=0, max_substeps=0,
         obs_stride=1, initial_state=None) -> Result:
     """rsv_run: the whole sequence, host inputs in, a Result out."""

@@ -1988,6 +1988,66 @@ void rsv_batch_destroy(rsv_batch* b) {
 // ---------------------------------------------------------------------------
 // Shot-to-shot noise: perturbed copies of one problem, occupations averaged.
 // ---------------------------------------------------------------------------
+// Many problems in one call: registers of at most kBatchMaxAtoms atoms share
+// one batched persistent launch (their results share the batch), larger ones
+// run on the streaming solver one by one.
+extern "C" rsv_status rsv_run_batch(rsv_ctx* ctx, const rsv_problem* problems, int32_t count,
+                                    const rsv_config* config, rsv_result** outs) {
+  g_last_error.clear();
+  if (!ctx || !problems || !config || !outs) return fail(RSV_ERR_INVALID_ARG, "NULL argument");
+  if (count < 1) return fail(RSV_ERR_INVALID_ARG, "count must be >= 1");
+  for (int i = 0; i < count; ++i) outs[i] = nullptr;
+  std::vector<int> small, large;
+  for (int i = 0; i < count; ++i) {
+    RSV_TRY(validate_problem(&problems[i]));
+    (problems[i].n_atoms <= kBatchMaxAtoms ? small : large).push_back(i);
+  }
+  auto release = [&](rsv_status st) {
+    for (int i = 0; i < count; ++i) {
+      if (outs[i]) rsv_result_free(outs[i]);
+      outs[i] = nullptr;
+    }
+    return st;
+  };
+  if (!small.empty()) {
+    std::vector<rsv_problem> probs;
+    for (int i : small) probs.push_back(problems[i]);
+    rsv_batch* b = nullptr;
+    rsv_status st = rsv_batch_create(ctx, probs.data(), (int32_t)probs.size(), config, &b);
+    if (st == RSV_OK) st = rsv_batch_run(b);
+    if (st != RSV_OK) {
+      if (b) rsv_batch_destroy(b);
+      return release(st);
+    }
+    std::shared_ptr<rsv_batch> holder(b, [](rsv_batch* p) { rsv_batch_destroy(p); });
+    for (size_t k = 0; k < small.size(); ++k) {
+      auto res = new rsv_result();
+      res->ctx = ctx;
+      res->n = probs[k].n_atoms;
+      res->precision = config->precision;
+      res->batch = holder;
+      res->index = (int)k;
+      int32_t rows = 0;
+      rsv_batch_occupations(b, (int32_t)k, nullptr, 0, &rows);
+      res->occ.resize((size_t)rows * res->n);
+      rsv_batch_occupations(b, (int32_t)k, res->occ.data(), rows, &rows);
+      res->rows = rows;
+      {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        ctx->results.insert(res);
+      }
+      outs[small[k]] = res;
+    }
+  }
+  rsv_config streaming = *config;
+  if (streaming.m_max < 0) streaming.m_max = 0;  // the depth autotuner is the batch's; the solver takes its default
+  for (int i : large) {
+    const rsv_status st = rsv_run(ctx, &problems[i], &streaming, &outs[i]);
+    if (st != RSV_OK) return release(st);
+  }
+  return RSV_OK;
+}
+
 extern "C" rsv_status rsv_run_shots(rsv_ctx* ctx, const rsv_problem* problem, const rsv_config* config,
                                     int32_t shots, const double* omega_scale, const double* delta_shift,
                                     const double* pos_shift_um, double* occ_mean, int32_t capacity_rows,

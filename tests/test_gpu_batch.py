@@ -155,6 +155,32 @@ def test_batch_alone_equals_in_mix(ctx):
     mix.close()
 
 
+def test_run_batch_mixes_batched_and_streaming(ctx):
+    """rsv_run_batch: the registers of at most 20 atoms share one batched
+    launch and match their complex128 streaming solves; the 21-atom problem
+    runs on the streaming solver and equals rsv_run exactly."""
+    probs = mixed_problems(31, [9, 21, 6, 12], 50)
+    res = api().run_batch(ctx, probs, 10, "c64", obs_stride=1)
+    assert len(res) == len(probs)
+    for r, p in zip(res, probs):
+        n = p.positions.shape[0]
+        if n <= 20:
+            s = api().Solver(ctx, p, 10, "c128", obs_stride=1)
+            s.run_to_end()
+            ref, occ_ref = s.state(), s.occupations()
+            s.close()
+            assert O.infidelity(r.state().astype(np.complex128), ref) <= 1e-5
+            assert np.max(np.abs(r.occupations() - occ_ref)) <= 1e-5
+        else:
+            one = api().run(ctx, p, 10, "c64", obs_stride=1)
+            assert np.array_equal(r.state(), one.state())
+            assert np.array_equal(r.occupations(), one.occupations())
+            one.close()
+        assert r.stats()["steps"] == 5
+    for r in res:
+        r.close()
+
+
 def test_batch_rejects_large_registers(ctx):
     rng = np.random.Generator(np.random.PCG64(3))
     big = W.random_knot_problem(rng, 21, 20)
