@@ -204,7 +204,8 @@ def reference_arm(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "c128 (f64)", "data": "synthetic",
-        "config": {"workload": WORKLOAD},
+        "config": {"workload": WORKLOAD, "n_atoms": N_ATOMS, "dt_ns": DT_NS, "m_max": M_MAX,
+                   "parallelism": "host cores (oracle)"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": f"step 0 (from |0...0>, the cheapest step) of the oracle's Lanczos "
                                    f"evolution (complex128, full re-orthogonalisation, tol 1e-7) on the first "
