@@ -17,6 +17,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <map>
+#include <future>
 #include <thread>
 #include <deque>
 #include <condition_variable>
@@ -2285,11 +2286,37 @@ extern "C" rsv_status rsv_gradient(rsv_ctx* ctx, const rsv_problem* problem, con
     for (double& v : neg_phi) v = -v;
     back.phi = neg_phi.data();
   }
+  // mu and nu evolve independently between nodes: each on its own stream,
+  // driven by its own host thread, joined before every generator pass
   rsv_solver *Bmu = nullptr, *Bnu = nullptr;
-  RSV_TRY(solver_create(ctx, &back, &cfg, nullptr, &Bmu));
-  held.solvers.push_back(Bmu);
-  RSV_TRY(solver_create(ctx, &back, &cfg, nullptr, &Bnu));
-  held.solvers.push_back(Bnu);
+  auto make_back = [&](rsv_solver** out) -> rsv_status {
+    cudaStream_t bs = nullptr;
+    RSV_CUDA(cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking));
+    const rsv_status c = solver_create(ctx, &back, &cfg, bs, out);
+    if (c != RSV_OK) {
+      cudaStreamDestroy(bs);
+      return c;
+    }
+    (*out)->own_stream = true;
+    held.solvers.push_back(*out);
+    return RSV_OK;
+  };
+  RSV_TRY(make_back(&Bmu));
+  RSV_TRY(make_back(&Bnu));
+  auto evolve_pair = [&](int k, double t) -> rsv_status {
+    auto nu_side = std::async(std::launch::async, [&, k, t] {
+      cudaSetDevice(ctx->device);
+      rsv_status r = Bnu->evolve(k, t);
+      if (r == RSV_OK && cudaStreamSynchronize(Bnu->stream) != cudaSuccess) r = RSV_ERR_CUDA;
+      return r;
+    });
+    rsv_status a = Bmu->evolve(k, t);
+    if (a == RSV_OK && cudaStreamSynchronize(Bmu->stream) != cudaSuccess) a = fail(RSV_ERR_CUDA, "stream sync failed");
+    const rsv_status b = nu_side.get();
+    RSV_TRY(a);
+    if (b != RSV_OK) return fail(b, "backward evolution of the state failed");
+    return RSV_OK;
+  };
   std::vector<double> gx, gw;
   gauss_legendre(kGradNodesPerPanel, gx, gw);
   int64_t nodes = 0, launches = 0;
@@ -2299,13 +2326,19 @@ extern "C" rsv_status rsv_gradient(rsv_ctx* ctx, const rsv_problem* problem, con
     cudaStream_t st = ctx->stream;
     const int grid = 4 * ctx->num_sms;
     // mu_K = O conj(psi_K); a vanishing costate leaves every derivative zero
-    RSV_CUDA(launch_conj_weight(ckpt[K], Bmu->d_psi, dim, c64, n, d_wbits, grid, st));
+    RSV_CUDA(launch_conj_weight(ckpt[K], Bmu->d_psi, dim, c64, n, d_wbits, grid, Bmu->stream));
     launches += 1;
     RSV_TRY(Bmu->observe_into_partials());
     RSV_TRY(Bmu->begin(0.0, 1, nullptr));
     RSV_TRY(Bmu->read_status());
     const bool live = Bmu->h_ks->norm2 > 0.0;
     std::vector<double> acc(6 * n);
+    cudaEvent_t read_done = nullptr;
+    RSV_CUDA(cudaEventCreateWithFlags(&read_done, cudaEventDisableTiming));
+    struct EventGuard {
+      cudaEvent_t e;
+      ~EventGuard() { cudaEventDestroy(e); }
+    } read_done_guard{read_done};
     for (int k = K - 1; k >= 0 && live; --k) {
       const double tau = sp[k].tau;
       const int P = panels > 0 ? panels : gradient_panels(sp[k], v_atoms, n);
@@ -2319,21 +2352,23 @@ extern "C" rsv_status rsv_gradient(rsv_ctx* ctx, const rsv_problem* problem, con
         }
       }
       nodes += (int64_t)s.size();
-      RSV_CUDA(launch_conj_weight(ckpt[k + 1], Bnu->d_psi, dim, c64, n, nullptr, grid, st));
+      RSV_CUDA(launch_conj_weight(ckpt[k + 1], Bnu->d_psi, dim, c64, n, nullptr, grid, Bnu->stream));
       launches += 1 + 2 * (int64_t)s.size();
       RSV_TRY(Bnu->observe_into_partials());
       RSV_CUDA(cudaMemsetAsync(d_acc, 0, sizeof(double) * 6 * n, st));
       double at = tau;
       for (int j = (int)s.size() - 1; j >= 0; --j) {
         const double step = at - s[j];
-        if (step > 0.0) {
-          RSV_TRY(Bmu->evolve(k, step));
-          RSV_TRY(Bnu->evolve(k, step));
-        }
+        if (step > 0.0) RSV_TRY(evolve_pair(k, step));
         at = s[j];
         RSV_CUDA(launch_generator(Bmu->d_psi, Bnu->d_psi, dim, c64, n, nchunks, d_gpart, w[j], d_acc, st));
+        // the next evolutions overwrite what this pass reads
+        RSV_CUDA(cudaEventRecord(read_done, st));
+        RSV_CUDA(cudaStreamWaitEvent(Bmu->stream, read_done, 0));
+        RSV_CUDA(cudaStreamWaitEvent(Bnu->stream, read_done, 0));
       }
       if (at > 0.0) RSV_TRY(Bmu->evolve(k, at));  // mu_k, the next step's costate
+      RSV_CUDA(cudaStreamSynchronize(Bmu->stream));
       RSV_CUDA(cudaMemcpyAsync(acc.data(), d_acc, sizeof(double) * 6 * n, cudaMemcpyDeviceToHost, st));
       RSV_CUDA(cudaStreamSynchronize(st));
       // the step's samples under the midpoint rule, weight 1/2 each
