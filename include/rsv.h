@@ -414,6 +414,16 @@ RSV_API rsv_status rsv_gradient(rsv_ctx* ctx, const rsv_problem* problem, const 
                                 const double* weights, int32_t panels, double* value_out, double* d_omega,
                                 double* d_delta, double* d_phi, int64_t* nodes_out, rsv_stats* stats_out);
 
+/* ---- diagnostics ------------------------------------------------------------ */
+
+/* Runs the error path of the library's bounded device waits: one kernel waits
+ * (with the same bounded wait the streaming passes use, limit 2 s) on a
+ * barrier that nothing completes, gives up, and sets an error word. Returns
+ * RSV_ERR_TIMEOUT with the message the solvers give for an aborted kernel; the
+ * context stays usable. RSV_OK would mean the wait did not give up. No fault
+ * or trap is raised. Synchronises the context stream (about 2 s). */
+RSV_API rsv_status rsv_check_bounded_wait(rsv_ctx* ctx);
+
 /* ---- open-system dynamics --------------------------------------------------- */
 
 /* The Lindblad master equation (Sec. III.A: open-system dynamics),

@@ -197,6 +197,10 @@ cudaError_t launch_multi_dot(const void* const* V, int nvec, const void* w, int6
 cudaError_t launch_multi_axpy(const void* const* V, const double* coef, int nvec, void* w, int64_t total, bool c64,
                               bool overwrite, int grid, double* partials, double* norm2_out, cudaStream_t stream);
 
+// Bounded-wait error path (wait_check_kernels.cu): sets *err after a wait on
+// a barrier that nothing completes gives up.
+cudaError_t launch_wait_check(int* err, cudaStream_t stream);
+
 // Sampling (sample_kernels.cu)
 cudaError_t launch_block_sums(const void* psi, int64_t dim, bool c64, int64_t chunk, double* sums, cudaStream_t stream);
 cudaError_t launch_sample(const void* psi, int64_t dim, bool c64, int64_t chunk, const double* chunk_cdf, int64_t nchunks,

@@ -2411,6 +2411,24 @@ extern "C" rsv_status rsv_gradient(rsv_ctx* ctx, const rsv_problem* problem, con
   return RSV_OK;
 }
 
+// The error path of the bounded device waits, end to end: a kernel waits on a
+// barrier nothing completes, gives up, sets an error word, and this call
+// reports RSV_ERR_TIMEOUT the way every streaming pass's caller does.
+extern "C" rsv_status rsv_check_bounded_wait(rsv_ctx* ctx) {
+  g_last_error.clear();
+  if (!ctx) return fail(RSV_ERR_INVALID_ARG, "NULL argument");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  cudaSetDevice(ctx->device);
+  int* d_err = reinterpret_cast<int*>(ctx->d_part);
+  int err = 0;
+  RSV_CUDA(cudaMemsetAsync(d_err, 0, sizeof(int), ctx->stream));
+  RSV_CUDA(launch_wait_check(d_err, ctx->stream));
+  RSV_CUDA(cudaMemcpyAsync(&err, d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  RSV_CUDA(cudaStreamSynchronize(ctx->stream));
+  if (err) return fail(RSV_ERR_TIMEOUT, "a device-side wait timed out (kernel aborted)");
+  return RSV_OK;
+}
+
 // Overlap <a|b> with |a|^2 and |b|^2 (fidelity with a target state).
 extern "C" rsv_status rsv_overlap(rsv_ctx* ctx, int32_t n_atoms, int32_t precision, const void* a_dev,
                                   const void* b_dev, double* out) {

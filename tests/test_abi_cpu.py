@@ -127,6 +127,7 @@ def test_overlap_and_gradient_reject_bad_arguments_without_a_gpu():
                             L._dptr(d_de), None, None, None) == -1
     assert b"NULL" in lib.rsv_last_error()
     assert lib.rsv_run_batch(None, C.byref(pa.struct), 1, C.byref(cfg), None) == -1
+    assert lib.rsv_check_bounded_wait(None) == -1
     rows = C.c_int32()
     assert lib.rsv_lindblad_run(None, C.byref(pa.struct), C.byref(cfg), None, None, None, None, None, 0,
                                 C.byref(rows), None) == -1
