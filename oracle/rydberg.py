@@ -302,6 +302,51 @@ def lanczos_expm(matvec, psi: np.ndarray, tau: float, tol: float = 1e-13, m_max:
     return psi, stats
 
 
+def chebyshev_expm(matvec, psi: np.ndarray, tau: float, e_min: float, e_max: float, tol: float = 1e-16):
+    """exp(-i tau H) psi by the Chebyshev expansion of Tal-Ezer and Kosloff
+    (J. Chem. Phys. 81, 3967 (1984)), an algorithm independent of Lanczos.
+
+    With the spectrum of H inside [e_min, e_max], H = a + b X with
+    a = (e_max + e_min) / 2, b = (e_max - e_min) / 2 and X's spectrum in
+    [-1, 1]; then exp(-i tau H) = e^{-i a tau} sum_k c_k (-i)^k J_k(b tau) T_k(X)
+    with c_0 = 1, c_k = 2, J_k the Bessel functions of the first kind and
+    T_k the Chebyshev polynomials (three-term recurrence on vectors). The sum
+    stops once k > b tau and |J_k(b tau)| < tol.
+    """
+    from scipy.special import jv
+    psi = np.asarray(psi, dtype=np.complex128)
+    a = 0.5 * (e_max + e_min)
+    b = 0.5 * (e_max - e_min)
+    if b <= 0.0:
+        return np.exp(-1j * a * tau) * psi
+    z = b * tau
+
+    def X(v):
+        return (matvec(v) - a * v) / b
+
+    t_prev, t_cur = psi, X(psi)
+    out = jv(0, z) * t_prev + 2.0 * (-1j) * jv(1, z) * t_cur
+    k = 1
+    while True:
+        k += 1
+        t_next = 2.0 * X(t_cur) - t_prev
+        jk = jv(k, z)
+        out = out + 2.0 * (-1j) ** k * jk * t_next
+        t_prev, t_cur = t_cur, t_next
+        if k > z and abs(jk) < tol:
+            break
+    return np.exp(-1j * a * tau) * out
+
+
+def spectral_bounds(V, omega_bar, delta_bar, E=None):
+    """Gershgorin interval of the Hamiltonian of Eq. (3): the diagonal range
+    widened by the largest off-diagonal row sum, sum_i Omega_i / 2."""
+    if E is None:
+        E = diagonal_energies(V, delta_bar)
+    r = 0.5 * float(np.sum(np.abs(omega_bar)))
+    return float(np.min(E)) - r, float(np.max(E)) + r
+
+
 def zero_state(n_atoms: int) -> np.ndarray:
     """|0...0> (Sec. II.B.2: the initial state of the QPU)."""
     psi = np.zeros(2 ** n_atoms, dtype=np.complex128)
@@ -345,7 +390,8 @@ def evolve(positions, c6, t_ns, dt_ns, omega, delta, phi=None, psi0=None,
            record_occupations: bool = True):
     """psi_K = exp(-i H_{K-1} tau) ... exp(-i H_0 tau) psi_0 (Eq. (6)).
 
-    method = "dense" (expm of the brute-force matrix, N <= 12) or "krylov".
+    method = "dense" (expm of the brute-force matrix, N <= 12), "krylov", or
+    "cheb" (Chebyshev expansion over the Gershgorin interval).
     Returns (psi_K, occ) where occ[k] = <n_i> after k steps (row 0 = psi_0).
     """
     V = pair_interactions(positions, c6)
@@ -356,6 +402,10 @@ def evolve(positions, c6, t_ns, dt_ns, omega, delta, phi=None, psi0=None,
         if method == "dense":
             H = dense_hamiltonian(V, om, de, ph)
             psi = scipy.linalg.expm(-1j * tau * H) @ psi
+        elif method == "cheb":
+            E = diagonal_energies(V, de)
+            lo, hi = spectral_bounds(V, om, de, E)
+            psi = chebyshev_expm(lambda x: apply_hamiltonian(x, V, om, de, ph, E), psi, tau, lo, hi)
         else:
             E = diagonal_energies(V, de)
             psi, _ = lanczos_expm(lambda x: apply_hamiltonian(x, V, om, de, ph, E), psi, tau,

@@ -595,3 +595,35 @@ def test_lindblad_state_stays_a_density_matrix():
         assert abs(np.trace(rho) - 1.0) <= 1e-13
         assert np.max(np.abs(rho - rho.conj().T)) <= 1e-14
         assert np.min(np.linalg.eigvalsh(0.5 * (rho + rho.conj().T))) >= -1e-13
+
+
+def test_dense_krylov_and_chebyshev_agree():
+    """Three independent evaluations of the same product of step exponentials
+    (scaling-and-squaring expm of the dense H, Lanczos, and the Chebyshev
+    expansion over the Gershgorin interval) agree, with phases and
+    time-dependent pulses; at 12 atoms without the dense path."""
+    rng = np.random.default_rng(3)
+    prob = W.random_knot_problem(rng, 6, 100, with_phi=True)
+    args = (prob.positions, prob.c6, prob.t_ns, 10, prob.omega, prob.delta, prob.phi)
+    a, _ = O.evolve(*args, method="dense")
+    b, _ = O.evolve(*args, method="cheb")
+    c, _ = O.evolve(*args, method="krylov", tol=1e-14)
+    assert O.norm_difference(a, b) <= 1e-13
+    assert O.norm_difference(a, c) <= 1e-13
+    prob = W.random_knot_problem(rng, 12, 20, with_phi=True)
+    args = (prob.positions, prob.c6, prob.t_ns, 10, prob.omega, prob.delta, prob.phi)
+    b, _ = O.evolve(*args, method="cheb")
+    c, _ = O.evolve(*args, method="krylov", tol=1e-14)
+    assert O.norm_difference(b, c) <= 1e-13
+
+
+def test_chebyshev_single_atom_closed_form():
+    """The Chebyshev path alone against the two-level closed form."""
+    om, de, ph, t = 5.0, 2.0, 0.4, 0.37
+    U = two_level_propagator(om, de, ph, t)
+    V = np.zeros((1, 1))
+    H = O.dense_hamiltonian(V, [om], [de], [ph])
+    lo, hi = O.spectral_bounds(V, np.array([om]), np.array([de]))
+    psi0 = np.array([0.6, 0.8j])
+    got = O.chebyshev_expm(lambda x: H @ x, psi0, t, lo, hi)
+    assert np.max(np.abs(got - U @ psi0)) <= 1e-14
