@@ -433,6 +433,18 @@ def norm_difference(a, b) -> float:
     return float(np.linalg.norm(np.asarray(a, np.complex128) - np.asarray(b, np.complex128)))
 
 
+def phase_min_norm_difference(a, b) -> float:
+    """min over theta of |a - e^{i theta} b|. Expanding the square,
+    |a|^2 + |b|^2 - 2 Re(e^{i theta} <a|b>) is smallest when e^{i theta} <a|b>
+    is real and positive, i.e. e^{i theta} = conj(<a|b>) / |<a|b>|; the norm is
+    then taken of the difference itself (no cancellation for close vectors)."""
+    a = np.asarray(a, dtype=np.complex128)
+    b = np.asarray(b, dtype=np.complex128)
+    ov = np.vdot(a, b)
+    phase = np.conj(ov) / abs(ov) if abs(ov) > 0.0 else 1.0
+    return float(np.linalg.norm(a - phase * b))
+
+
 # ---------------------------------------------------------------------------
 # Sampling: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) + inverse CDF
 # ---------------------------------------------------------------------------

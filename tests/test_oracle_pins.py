@@ -627,3 +627,18 @@ def test_chebyshev_single_atom_closed_form():
     psi0 = np.array([0.6, 0.8j])
     got = O.chebyshev_expm(lambda x: H @ x, psi0, t, lo, hi)
     assert np.max(np.abs(got - U @ psi0)) <= 1e-14
+
+
+def test_phase_minimised_norm_difference():
+    """Against brute force over a fine grid of global phases, and zero for a
+    pure phase."""
+    rng = np.random.default_rng(12)
+    a = rng.normal(size=16) + 1j * rng.normal(size=16)
+    b = a + 0.05 * (rng.normal(size=16) + 1j * rng.normal(size=16))
+    b = b * np.exp(0.7j)
+    got = O.phase_min_norm_difference(a, b)
+    grid = min(np.linalg.norm(a - np.exp(1j * t) * b) for t in np.linspace(0, 2 * math.pi, 200001))
+    assert got <= grid + 1e-12
+    assert grid - got <= 1e-6
+    assert O.phase_min_norm_difference(a, np.exp(-1.3j) * a) <= 1e-13
+    assert O.norm_difference(a, np.exp(-1.3j) * a) > 1.0
