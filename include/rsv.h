@@ -362,8 +362,9 @@ RSV_API rsv_status rsv_run_shots(rsv_ctx* ctx, const rsv_problem* problem, const
                                  const double* omega_scale, const double* delta_shift, const double* pos_shift_um,
                                  double* occ_mean, int32_t capacity_rows, int32_t* n_rows);
 
-/* Solves `count` problems with one config and returns one result per
- * problem in outs[count] (each freed with rsv_result_free). Problems of at
+/* Solves `count` problems with one config (each the evolution of Eq. (6),
+ * Sec. III) and returns one result per problem in outs[count] (each freed
+ * with rsv_result_free). Problems of at
  * most 20 atoms are evolved together by one batched persistent launch
  * (rsv_batch_*; their results share it, and it is freed with the last of
  * them). Larger problems run on the streaming solver one after another, with
