@@ -38,8 +38,9 @@ def api():
 
 
 def oracle_evolve(prob, dt, psi0=None):
+    # the oracle's Chebyshev path (pinned to its Lanczos and dense paths)
     return O.evolve(prob.positions, prob.c6, prob.t_ns, dt, prob.omega, prob.delta, prob.phi, psi0=psi0,
-                    method="krylov", tol=1e-14)
+                    method="cheb")
 
 
 def mixed_problems(seed, sizes, t_ns, with_phi=False):

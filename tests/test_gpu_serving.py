@@ -101,7 +101,7 @@ def test_served_result_matches_oracle(ctx):
     srv = api().Server(ctx, slots=2)
     t = srv.submit(p, 10, "c128", obs_stride=1)
     r = srv.poll(t)
-    ref, occ_ref = O.evolve(p.positions, p.c6, p.t_ns, 10, p.omega, p.delta, p.phi, method="krylov", tol=1e-14)
+    ref, occ_ref = O.evolve(p.positions, p.c6, p.t_ns, 10, p.omega, p.delta, p.phi, method="cheb")
     assert O.infidelity(r.state(), ref) <= 1e-10
     assert np.max(np.abs(r.occupations() - occ_ref)) <= 1e-10
     r.close()

@@ -35,7 +35,7 @@ def oracle_mean(prob, dt, scale, shift, pos_shift):
     for k in range(len(scale)):
         pos = prob.positions + (pos_shift[k] if pos_shift is not None else 0.0)
         _, occ = O.evolve(pos, prob.c6, prob.t_ns, dt, prob.omega * scale[k], prob.delta + shift[k], prob.phi,
-                          method="krylov", tol=1e-14)
+                          method="cheb")  # the oracle's Chebyshev path (pinned to its Lanczos path)
         rows.append(np.asarray(occ))
     return np.mean(rows, axis=0)
 
