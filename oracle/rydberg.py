@@ -20,7 +20,15 @@ What it computes (arXiv 2510.09813):
   * Lanczos (Krylov) evaluation of exp(-i H dt) psi (Sec. III.A), here with full
     re-orthogonalisation and a tight tolerance so that it reproduces the exact
     product of exponentials; a dense expm path (N <= 12) is the brute-force check.
-  * Observables <n_i> and bitstring sampling (the emulator results of Sec. III).
+  * Observables <n_i> and bitstring sampling (the emulator results of Sec. III),
+    pair correlations, energy moments and overlaps with a target state.
+  * An independent Chebyshev propagator (Tal-Ezer and Kosloff) for the same
+    product of step exponentials.
+  * Exact gradients of occupation observables with respect to the pulse
+    samples (Sec. V: the emulator is differentiable), by Frechet derivatives
+    of the step exponentials.
+  * The Lindblad master equation on the dense superoperator (Sec. III.A,
+    open-system dynamics) with Rydberg dephasing and spontaneous decay.
 
 Readings of points the paper leaves open are listed where they are used.
 """
