@@ -250,7 +250,12 @@ RSV_API rsv_status rsv_sample(rsv_ctx* ctx, int32_t n_atoms, int32_t precision, 
  * load the library's device code): make it before any stream capture. Calls
  * that overlap on one device (other threads or streams, before the previous
  * call's work has finished) share the array and race: order them on one
- * stream or serialise them. */
+ * stream or serialise them. The looked-up address is kept for the life of the
+ * process: do not use this entry on a device after cudaDeviceReset (or any
+ * other re-creation of its primary context), whose array then lives at a new
+ * address. psi_dev or out_dev that is not device memory of the current device
+ * is rejected with RSV_ERR_INVALID_ARG (checked with
+ * cudaPointerGetAttributes, which allocates nothing). */
 RSV_API rsv_status rsv_observe_static(int32_t n_atoms, int32_t precision, const void* psi_dev, double* out_dev,
                                       void* cuda_stream);
 
@@ -383,6 +388,12 @@ RSV_API rsv_status rsv_run_batch(rsv_ctx* ctx, const rsv_problem* problems, int3
  * Synchronises the context stream. */
 RSV_API rsv_status rsv_overlap(rsv_ctx* ctx, int32_t n_atoms, int32_t precision, const void* a_dev,
                                const void* b_dev, double* out);
+/* Fidelity of two device states (Sec. III results: fidelity with a target):
+ * *out = |<a|b>|^2 / (|a|^2 |b|^2), from the sums of rsv_overlap (host
+ * double). Arguments as for rsv_overlap; RSV_ERR_INVALID_ARG if either state
+ * has zero norm. Synchronises the context stream. */
+RSV_API rsv_status rsv_fidelity(rsv_ctx* ctx, int32_t n_atoms, int32_t precision, const void* a_dev,
+                                const void* b_dev, double* out);
 
 /* Value and gradient of an occupation observable at the end of the sequence,
  * <O>(T) = <psi_K| sum_i weights[i] n_i |psi_K> (psi_K unnormalised, as
@@ -489,7 +500,18 @@ RSV_API rsv_status rsv_submit(rsv_server* srv, const rsv_problem* problem, const
  * retired), RSV_ERR_TIMEOUT if still queued or running, RSV_ERR_NOT_FOUND for
  * an unknown or retired ticket, or the solve's own error code. */
 RSV_API rsv_status rsv_poll(rsv_server* srv, uint64_t ticket, int32_t timeout_ms, rsv_result** out);
-/* Current load: queued and running requests, device bytes held by running ones. */
+/* The device footprint a server charges for one request (Sec. III.A.1 memory
+ * accounting): the bytes its solver allocates (state, m_max Krylov vectors,
+ * two work vectors, per-tile diagonal rows, tables, per-step parameters and
+ * occupation rows), with the config's defaults applied. Host-only. */
+RSV_API rsv_status rsv_request_bytes(const rsv_problem* problem, const rsv_config* config, size_t* out);
+/* Current load: queued and running requests, and the device bytes charged to
+ * the server's memory: the footprints of running solves plus what finished,
+ * unfreed results still hold. A finished streaming solve keeps only its state
+ * (2^n amplitudes; the rest goes back at once) until rsv_result_free; a
+ * batched group keeps its whole footprint until its last result is freed.
+ * Results held unfreed therefore delay later admissions, never overrun the
+ * memory. */
 RSV_API rsv_status rsv_server_load(rsv_server* srv, int32_t* queued, int32_t* running, size_t* bytes_in_use);
 /* Cancels queued requests, waits for running ones, frees unclaimed results. */
 RSV_API void rsv_server_destroy(rsv_server* srv);

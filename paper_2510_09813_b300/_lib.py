@@ -95,6 +95,8 @@ def lib():
                                     C.POINTER(I32)]),
             "rsv_sample": (I32, [P, I32, I32, P, I64, U64, C.POINTER(C.c_uint64)]),
             "rsv_overlap": (I32, [P, I32, I32, P, P, PD]),
+            "rsv_fidelity": (I32, [P, I32, I32, P, P, PD]),
+            "rsv_request_bytes": (I32, [C.POINTER(Problem_), C.POINTER(Config_), C.POINTER(SZ)]),
             "rsv_check_bounded_wait": (I32, [P]),
             "rsv_run_batch": (I32, [P, C.POINTER(Problem_), I32, C.POINTER(Config_), C.POINTER(P)]),
             "rsv_lindblad_run": (I32, [P, C.POINTER(Problem_), C.POINTER(Config_), PD, PD, P, P, PD, I32,

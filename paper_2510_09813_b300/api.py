@@ -485,9 +485,22 @@ def overlap(ctx: Context, n_atoms: int, precision, a, b) -> tuple[complex, float
 
 
 def fidelity(ctx: Context, n_atoms: int, precision, target, psi) -> float:
-    """|<target|psi>|^2 / (|target|^2 |psi|^2)."""
-    ov, aa, bb = overlap(ctx, n_atoms, precision, target, psi)
-    return abs(ov) ** 2 / (aa * bb)
+    """|<target|psi>|^2 / (|target|^2 |psi|^2) of two CUDA state tensors (rsv_fidelity)."""
+    out = C.c_double()
+    check(L.lib().rsv_fidelity(ctx.handle, int(n_atoms), precision_code(precision),
+                               _check_state(target, n_atoms, precision), _check_state(psi, n_atoms, precision),
+                               C.byref(out)))
+    return out.value
+
+
+def request_bytes(problem, dt_ns: int, precision="c64", krylov_tol=0.0, m_max=0, max_substeps=0,
+                  obs_stride=1) -> int:
+    """rsv_request_bytes: the device footprint a server charges for this request."""
+    pa = L.ProblemArgs.from_problem(problem)
+    cfg = L.make_config(dt_ns, precision, krylov_tol, m_max, max_substeps, obs_stride)
+    out = C.c_size_t()
+    check(L.lib().rsv_request_bytes(C.byref(pa.struct), C.byref(cfg), C.byref(out)))
+    return out.value
 
 
 class Gradient:

@@ -364,7 +364,9 @@ bool any_phi(const std::vector<StepParams>& sp, int n) {
 // row locality against the L2 reuse distance of those partners. Candidates
 // c in {4, 5} x f1_fast in {0, 2, 4} are timed on the caller's buffers (the pass
 // only reads x and read-modify-writes z, whose contents do not matter here) and
-// the fastest is cached per (n_atoms, precision). RSV_SEGMENT_BITS fixes c.
+// the fastest is cached per (n_atoms, precision). RSV_SEGMENT_BITS fixes c,
+// and with it RSV_TILE_ORDER_BITS fixes f1_fast (default 0): a plan override
+// that skips the tuner (tests force every candidate shape this way).
 int segment_override() {
   const char* e = std::getenv("RSV_SEGMENT_BITS");
   if (!e) return 0;
@@ -372,16 +374,38 @@ int segment_override() {
   return (v >= 2 && v <= 8) ? v : 0;
 }
 
+int tile_order_override() {
+  const char* e = std::getenv("RSV_TILE_ORDER_BITS");
+  if (!e) return 0;
+  const int v = std::atoi(e);
+  return (v >= 0 && v <= 8) ? v : 0;
+}
+
+// A strided-pass shape the kernels accept for this register.
+bool shape_valid(int n, bool c64, int num_sms, int seg, int f1f) {
+  const Plan p = make_plan(n, c64, num_sms, seg, f1f);
+  return !p.two_pass || (p.b.nG <= kMaxGBits && p.b.c >= (c64 ? 1 : 0));
+}
+
+// The overridden shape (seg_bits * 16 + f1_fast), or 0 when none is set or
+// the one set does not fit this register.
+int shape_override(int n, bool c64, int num_sms) {
+  const int o = segment_override();
+  if (!o) return 0;
+  const int f = tile_order_override();
+  return shape_valid(n, c64, num_sms, o, f) ? o * 16 + f : 0;
+}
+
 // Tuned shape packed as seg_bits * 16 + f1_fast.
 int shape_for(rsv_ctx* ctx, int n, bool c64) {
-  if (const int o = segment_override()) return o * 16;
+  if (const int o = shape_override(n, c64, ctx->num_sms)) return o;
   auto it = ctx->tuned_segment.find({n, c64 ? 1 : 0});
   return it == ctx->tuned_segment.end() ? kMinSegmentBits * 16 : it->second;
 }
 
 int tune_shape(rsv_ctx* ctx, cudaStream_t stream, int n, bool c64, StepParams* sp, double* vmat, KState* ks, double* part, void* x,
                void* z) {
-  if (const int o = segment_override()) return o * 16;
+  if (const int o = shape_override(n, c64, ctx->num_sms)) return o;
   const auto key = std::make_pair(n, c64 ? 1 : 0);
   auto it = ctx->tuned_segment.find(key);
   if (it != ctx->tuned_segment.end()) return it->second;
@@ -508,6 +532,29 @@ struct rsv_solver {
     RSV_TRY(ctx->arena.alloc(bytes, out));
     owned.push_back(*out);
     return RSV_OK;
+  }
+  // Arena bytes of the state allocation (the arena rounds to 256 bytes).
+  size_t state_alloc_bytes() const { return ((size_t)dim * amp_bytes(precision) + 255) & ~size_t(255); }
+  // A finished solve kept only for its final state: returns every other
+  // device allocation to the arena. The solver can no longer step.
+  bool trimmed = false;
+  void trim_to_state() {
+    cudaStreamSynchronize(stream);
+    for (void* p : owned)
+      if (p != d_psi) ctx->arena.release(p);
+    owned.assign(1, d_psi);
+    d_sp = nullptr;
+    d_vmat = nullptr;
+    d_qtab = nullptr;
+    d_diag = nullptr;
+    d_u[0] = d_u[1] = nullptr;
+    basis.clear();
+    d_basis = nullptr;
+    d_ks = nullptr;
+    d_part = nullptr;
+    d_cpart = nullptr;
+    d_occ = nullptr;
+    trimmed = true;
   }
   ~rsv_solver() {
     if (ctx) cudaStreamSynchronize(stream);
@@ -715,6 +762,23 @@ struct rsv_solver {
 // ---------------------------------------------------------------------------
 // Result
 // ---------------------------------------------------------------------------
+// Admission accounting of a server, shared with the results it hands out:
+// bytes admitted and not yet released, guarded by `mu`, whose waiters (the
+// server's workers) are woken on `cv_work` whenever bytes are released. It
+// outlives the server while any of its results is unfreed.
+struct ServeLedger {
+  std::mutex mu;
+  std::condition_variable cv_work;
+  size_t in_use = 0;
+  void release(size_t bytes) {
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      in_use -= bytes;
+    }
+    cv_work.notify_all();
+  }
+};
+
 struct rsv_result {
   rsv_ctx* ctx = nullptr;
   int n = 0, precision = 0;
@@ -725,6 +789,11 @@ struct rsv_result {
   int rows = 0;
   double wait_s = 0.0;     // served requests: submission to admission
   double service_s = 0.0;  // admission (or call) to completion
+  // served requests: device bytes the result still holds, charged to the
+  // server's admission budget until rsv_result_free (a batched group's charge
+  // rides on the shared batch instead and is released with it)
+  std::shared_ptr<ServeLedger> ledger;
+  size_t charged = 0;
 };
 
 // A prepared H (Eq. (3)) for repeated y = H x: tables and per-tile diagonal
@@ -1378,6 +1447,7 @@ void rsv_solver_destroy(rsv_solver* s) {
 // Advances a solver on its own stream. Callers serialise access to `s`; the
 // context lock is not needed (the arena has its own).
 static rsv_status solver_step(rsv_solver* s, int32_t n_steps) {
+  if (s->trimmed) return fail(RSV_ERR_INVALID_ARG, "the solve has finished and kept only its state");
   cudaSetDevice(s->ctx->device);
   const auto t0 = std::chrono::steady_clock::now();
   for (int i = 0; i < n_steps && s->done < s->nsteps; ++i) RSV_TRY(s->step_once());
@@ -1570,7 +1640,8 @@ void rsv_result_free(rsv_result* r) {
     r->ctx->results.erase(r);
   }
   delete r->solver;  // owned by the result, not in the context's solver set
-  delete r;          // a batch goes with its last result
+  if (r->ledger) r->ledger->release(r->charged);
+  delete r;          // a batch goes with its last result (and releases its group's charge)
 }
 
 }  // extern "C"
@@ -2453,6 +2524,17 @@ extern "C" rsv_status rsv_overlap(rsv_ctx* ctx, int32_t n_atoms, int32_t precisi
   return RSV_OK;
 }
 
+// Fidelity |<a|b>|^2 / (|a|^2 |b|^2) from the overlap sums.
+extern "C" rsv_status rsv_fidelity(rsv_ctx* ctx, int32_t n_atoms, int32_t precision, const void* a_dev,
+                                   const void* b_dev, double* out) {
+  if (!out) return fail(RSV_ERR_INVALID_ARG, "NULL argument");
+  double ov[4];
+  RSV_TRY(rsv_overlap(ctx, n_atoms, precision, a_dev, b_dev, ov));
+  if (!(ov[2] > 0.0) || !(ov[3] > 0.0)) return fail(RSV_ERR_INVALID_ARG, "a state has zero norm");
+  *out = (ov[0] * ov[0] + ov[1] * ov[1]) / (ov[2] * ov[3]);
+  return RSV_OK;
+}
+
 // ---------------------------------------------------------------------------
 // Open-system dynamics (Sec. III.A): the Lindblad master equation, evolved
 // step by step with the midpoint pulses of Sec. III by a Krylov exponential of
@@ -2798,10 +2880,15 @@ struct rsv_server {
   rsv_ctx* ctx = nullptr;
   int slots = 0;
   int batch_atoms = 0;  // 0: every request on the streaming solver
-  size_t budget = 0, in_use = 0;
+  size_t budget = 0;
+  // admitted bytes: running requests' footprints plus what finished results
+  // still hold until they are freed (shared with those results)
+  std::shared_ptr<ServeLedger> ledger = std::make_shared<ServeLedger>();
+  size_t& in_use = ledger->in_use;
+  std::mutex& mu = ledger->mu;
+  std::condition_variable& cv_work = ledger->cv_work;
   double max_bypass_s = 0.5;
-  std::mutex mu;
-  std::condition_variable cv_work, cv_done;
+  std::condition_variable cv_done;
   std::deque<ServeRequest*> queue;
   std::map<uint64_t, std::unique_ptr<ServeRequest>> reqs;
   uint64_t next_ticket = 1;
@@ -2833,9 +2920,16 @@ struct rsv_server {
     return a->prob.n_atoms == b->prob.n_atoms && std::memcmp(&a->cfg, &b->cfg, sizeof(rsv_config)) == 0;
   }
 
-  rsv_status serve_group(const std::vector<ServeRequest*>& g, std::vector<rsv_result*>& out) {
+  // Solves a group of like requests in one batched launch. On success the
+  // group's footprint stays charged until its last result is freed (the
+  // shared batch's deleter releases it); `charged_out` is set to that sum.
+  rsv_status serve_group(const std::vector<ServeRequest*>& g, std::vector<rsv_result*>& out, size_t* charged_out) {
     std::vector<rsv_problem> probs;
-    for (const ServeRequest* q : g) probs.push_back(q->prob);
+    size_t group_bytes = 0;
+    for (const ServeRequest* q : g) {
+      probs.push_back(q->prob);
+      group_bytes += q->bytes;
+    }
     rsv_batch* b = nullptr;
     rsv_status st = rsv_batch_create(ctx, probs.data(), (int32_t)g.size(), &g[0]->cfg, &b);
     if (st == RSV_OK) st = batch_run(b, false);
@@ -2843,7 +2937,12 @@ struct rsv_server {
       if (b) rsv_batch_destroy(b);
       return st;
     }
-    std::shared_ptr<rsv_batch> holder(b, [](rsv_batch* p) { rsv_batch_destroy(p); });
+    std::shared_ptr<ServeLedger> led = ledger;
+    std::shared_ptr<rsv_batch> holder(b, [led, group_bytes](rsv_batch* p) {
+      rsv_batch_destroy(p);
+      led->release(group_bytes);
+    });
+    *charged_out = group_bytes;
     for (size_t i = 0; i < g.size(); ++i) {
       auto res = new rsv_result();
       res->ctx = ctx;
@@ -2880,7 +2979,13 @@ struct rsv_server {
       rsv_solver_destroy(s);
       return k;
     }
-    return make_result(s, out);
+    RSV_TRY(make_result(s, out));
+    // the result only needs the final state: give the Krylov basis, work
+    // vectors and tables back now, and keep the state charged until it is freed
+    s->trim_to_state();
+    (*out)->ledger = ledger;
+    (*out)->charged = s->state_alloc_bytes();
+    return RSV_OK;
   }
 
   void worker() {
@@ -2916,7 +3021,8 @@ struct rsv_server {
         running += (int)g.size();
       }
       std::vector<rsv_result*> res(g.size(), nullptr);
-      const rsv_status st = batchable(g[0]) ? serve_group(g, res) : serve(g[0], &res[0]);
+      size_t group_charge = 0;  // equals the sum of the group's footprints
+      const rsv_status st = batchable(g[0]) ? serve_group(g, res, &group_charge) : serve(g[0], &res[0]);
       const std::string err = st == RSV_OK ? std::string() : g_last_error;
       {
         std::lock_guard<std::mutex> lk(mu);
@@ -2932,7 +3038,12 @@ struct rsv_server {
             res[i]->service_s = q->t_done - q->t_admit;
           }
           q->state = 2;
-          in_use -= q->bytes;
+          // bytes a result keeps stay charged until it is freed: the state of
+          // a streaming result; a batched group's whole footprint, which the
+          // shared batch's deleter releases with the group's last result
+          const bool group_held = batchable(g[0]) && st == RSV_OK;
+          const size_t kept = group_held ? q->bytes : (res[i] ? res[i]->charged : 0);
+          in_use -= q->bytes - kept;
           --running;
         }
       }
@@ -3048,6 +3159,20 @@ rsv_status rsv_poll(rsv_server* srv, uint64_t ticket, int32_t timeout_ms, rsv_re
   return RSV_OK;
 }
 
+rsv_status rsv_request_bytes(const rsv_problem* problem, const rsv_config* config, size_t* out) {
+  g_last_error.clear();
+  if (!config || !out) return fail(RSV_ERR_INVALID_ARG, "NULL argument");
+  RSV_TRY(validate_problem(problem));
+  rsv_config cfg = *config;
+  if (cfg.dt_ns < 1) return fail(RSV_ERR_INVALID_ARG, "dt_ns must be >= 1");
+  if (cfg.precision != RSV_C64 && cfg.precision != RSV_C128) return fail(RSV_ERR_INVALID_ARG, "bad precision");
+  if (cfg.m_max == 0) cfg.m_max = 30;
+  if (cfg.m_max < 2 || cfg.m_max > kMaxKrylov) return fail(RSV_ERR_INVALID_ARG, "m_max must be in [2, 64]");
+  if (cfg.obs_stride < 0) return fail(RSV_ERR_INVALID_ARG, "obs_stride must be >= 0");
+  *out = solver_bytes(problem, cfg);
+  return RSV_OK;
+}
+
 rsv_status rsv_server_load(rsv_server* srv, int32_t* queued, int32_t* running, size_t* bytes_in_use) {
   if (!srv) return fail(RSV_ERR_INVALID_ARG, "NULL server");
   std::lock_guard<std::mutex> lk(srv->mu);
@@ -3158,6 +3283,19 @@ rsv_status rsv_observe_static(int32_t n_atoms, int32_t precision, const void* ps
   RSV_CUDA(cudaGetDevice(&device));
   if (device < 0 || device >= kStaticMaxDevices)
     return fail(RSV_ERR_INVALID_ARG, "rsv_observe_static: device index beyond " + std::to_string(kStaticMaxDevices - 1));
+  // both buffers must be device memory of the current device: a kernel given
+  // another device's (or host) memory would fault or read the wrong bytes
+  for (const void* p : {psi_dev, static_cast<const void*>(out_dev)}) {
+    cudaPointerAttributes pa{};
+    if (cudaPointerGetAttributes(&pa, p) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(RSV_ERR_INVALID_ARG, "rsv_observe_static: a buffer is not CUDA memory");
+    }
+    const bool dev_mem = pa.type == cudaMemoryTypeDevice || pa.type == cudaMemoryTypeManaged;
+    if (!dev_mem || pa.device != device)
+      return fail(RSV_ERR_INVALID_ARG, "rsv_observe_static: psi_dev and out_dev must be device memory of the "
+                                       "current device " + std::to_string(device));
+  }
   unsigned char* scratch = nullptr;
   int sms = 0;
   RSV_TRY(static_scratch(device, &scratch, &sms));

@@ -131,3 +131,20 @@ def test_overlap_and_gradient_reject_bad_arguments_without_a_gpu():
     rows = C.c_int32()
     assert lib.rsv_lindblad_run(None, C.byref(pa.struct), C.byref(cfg), None, None, None, None, None, 0,
                                 C.byref(rows), None) == -1
+
+
+def test_request_bytes_is_footprint_plus_sequence():
+    """The server's charge for a request: rsv_footprint_bytes plus the per-step
+    parameters and occupation rows, each rounded to 256 bytes (host-only)."""
+    rng = np.random.Generator(np.random.PCG64(3))
+    p = W.random_knot_problem(rng, 12, 100)
+    base = api.footprint_bytes(12, "c64", 30)
+    b1 = api.request_bytes(p, 10, "c64", obs_stride=0)
+    b2 = api.request_bytes(p, 10, "c64", obs_stride=1)
+    b3 = api.request_bytes(p, 5, "c64", obs_stride=0)
+    assert base < b1 < b2 and b1 < b3
+    assert (b1 - base) % 256 == 0 and (b2 - base) % 256 == 0
+    # 10 steps of 10 ns (obs_stride 1: 12 rows of 12 doubles)
+    assert b2 - b1 == ((8 * 12 * 12 + 255) // 256 - (8 * 12 * 2 + 255) // 256) * 256
+    with pytest.raises(api.RsvError):
+        api.request_bytes(p, 0, "c64")

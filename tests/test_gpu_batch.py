@@ -187,3 +187,21 @@ def test_batch_rejects_large_registers(ctx):
     big = W.random_knot_problem(rng, 21, 20)
     with pytest.raises(api().RsvError, match="batched limit"):
         api().Batch(ctx, [big], 10, "c64")
+
+
+@pytest.mark.parametrize("prec", ["c64", "c128"])
+def test_batch_autotuned_depth(ctx, prec):
+    """m_max < 0: the batch times its Krylov-depth candidates on a sample of
+    the registers and keeps one of them; the registers then match the oracle."""
+    sizes = [10, 16, 12, 14, 11, 15, 13, 10, 16, 12, 14, 11]
+    probs = mixed_problems(51, sizes, 120)
+    b = api().Batch(ctx, probs, 10, prec, m_max=-1, obs_stride=1)
+    b.run()
+    st = b.stats()
+    assert st["krylov_dim_max"] in (12, 16, 20, 24, 32, 40)
+    for i in (0, 1, 5, 11):
+        ref, occ_ref = oracle_evolve(probs[i], 10)
+        psi = b.state(i).astype(np.complex128)
+        assert O.infidelity(psi, ref) <= INFID_TOL[prec], i
+        assert np.max(np.abs(b.occupations(i) - occ_ref)) <= OCC_TOL[prec]
+    b.close()

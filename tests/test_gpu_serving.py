@@ -51,9 +51,21 @@ def test_results_alone_equal_in_mix(ctx):
     requests that run concurrently on their own streams."""
     reqs = requests(21, [14, 9, 20, 12, 17, 11, 22, 15, 8, 19, 13, 16, 12, 12, 9, 9])
     srv = api().Server(ctx, slots=4)
-    tickets = [srv.submit(p, 10, prec, obs_stride=1) for p, prec in reqs]
+    t_sub, tickets = [], []
+    for p, prec in reqs:
+        t_sub.append(time.perf_counter())
+        tickets.append(srv.submit(p, 10, prec, obs_stride=1))
     results = [srv.poll(t, timeout_ms=-1) for t in tickets]
     srv.close()
+    # the mix really ran concurrently: service intervals [admission, completion]
+    # (host submission time + the server's wait and service times) overlap
+    spans = []
+    for ts, r in zip(t_sub, results):
+        w, sv = r.times()
+        spans.append((ts + w, ts + w + sv))
+    overlaps = sum(1 for i in range(len(spans)) for j in range(i + 1, len(spans))
+                   if min(spans[i][1], spans[j][1]) - max(spans[i][0], spans[j][0]) > 1e-3)
+    assert overlaps >= 3, spans
     for (p, prec), r in zip(reqs, results):
         one = api().Server(ctx, slots=1)
         alone = one.poll(one.submit(p, 10, prec, obs_stride=1))
@@ -161,4 +173,63 @@ def test_errors(ctx):
         srv.poll(t, 0)  # retired once claimed
     assert e.value.code == -7
     r.close()
+    srv.close()
+
+
+def test_running_count_shows_concurrency(ctx):
+    """While a burst is served by 4 slots, the server reports more than one
+    solve running at the same time."""
+    reqs = requests(23, [20, 20, 20, 20, 20, 20], t_lo=150, t_hi=200)
+    srv = api().Server(ctx, slots=4)
+    peak = {"running": 0}
+    stop = threading.Event()
+
+    def sample():
+        while not stop.is_set():
+            peak["running"] = max(peak["running"], srv.load()[1])
+            time.sleep(0.0005)
+
+    th = threading.Thread(target=sample)
+    th.start()
+    tickets = [srv.submit(p, 10, prec, obs_stride=0) for p, prec in reqs]
+    results = [srv.poll(t) for t in tickets]
+    stop.set()
+    th.join()
+    assert peak["running"] >= 2
+    for r in results:
+        r.close()
+    srv.close()
+
+
+def test_unfreed_results_delay_admission(ctx):
+    """A finished result keeps its state charged to the server's memory until
+    it is freed: with room for one solve plus half a state, the next request
+    waits (it does not fail) while the first result is held, and runs once
+    that result is freed. The charge of a held result is its state alone."""
+    A = api()
+    rng = np.random.Generator(np.random.PCG64(41))
+    p1 = W.random_knot_problem(rng, 16, 60)
+    p2 = W.random_knot_problem(rng, 16, 60)
+    need = A.request_bytes(p1, 10, "c128", m_max=4, obs_stride=0)
+    assert need == A.request_bytes(p2, 10, "c128", m_max=4, obs_stride=0)
+    state = (2 ** 16) * 16
+    srv = A.Server(ctx, slots=2, memory_bytes=need + state // 2, max_bypass_s=-1)
+    r1 = srv.poll(srv.submit(p1, 10, "c128", m_max=4, obs_stride=0))
+    q, running, held = srv.load()
+    assert running == 0 and held == state
+    t2 = srv.submit(p2, 10, "c128", m_max=4, obs_stride=0)
+    assert srv.poll(t2, 300) is None  # waits behind the held state
+    q, running, held = srv.load()
+    assert q == 1 and running == 0
+    ref1 = A.run(ctx, p1, 10, "c128", m_max=4, obs_stride=0)
+    assert np.array_equal(r1.state(), ref1.state())  # the held state is intact
+    r1.close()
+    r2 = srv.poll(t2, -1)
+    assert r2 is not None
+    ref2 = A.run(ctx, p2, 10, "c128", m_max=4, obs_stride=0)
+    assert np.array_equal(r2.state(), ref2.state())
+    r2.close()
+    assert srv.load()[2] == 0
+    for x in (ref1, ref2):
+        x.close()
     srv.close()

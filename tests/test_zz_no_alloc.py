@@ -93,3 +93,10 @@ def test_static_rejects_beyond_limit(ctx):
     assert lib.rsv_observe_static(4, L.RSV_C64, None, o, None) == -1
     assert lib.rsv_observe_static(4, L.RSV_C64, p, C.c_void_p(out.data_ptr() + 4), None) == -1
     assert lib.rsv_observe_static(4, L.RSV_C64, C.c_void_p(psi.data_ptr() + 8), o, None) == -1
+    # host memory in place of a device buffer is refused before any launch
+    host = np.zeros(40)
+    h = C.c_void_p(host.ctypes.data)
+    assert lib.rsv_observe_static(4, L.RSV_C64, p, h, None) == -1
+    assert "device memory of the current device" in lib.rsv_last_error().decode()
+    hpsi = np.zeros(2 ** 4, dtype=np.complex64)
+    assert lib.rsv_observe_static(4, L.RSV_C64, C.c_void_p(hpsi.ctypes.data), o, None) == -1
