@@ -144,7 +144,7 @@ def kernel_source_hash():
     it includes, and its argument struct."""
     csrc = os.path.join(ROOT, "paper_2510_09813_b300", "csrc")
     h = hashlib.sha256()
-    for f in ("tile_kernels.cu", "vec_ops.cuh", "tma.cuh", "rsv_common.cuh"):
+    for f in ("tile_kernels.cu", "strided_kernels.cu", "vec_ops.cuh", "tma.cuh", "rsv_common.cuh"):
         h.update(open(os.path.join(csrc, f), "rb").read())
     hdr = open(os.path.join(csrc, "kernels.h")).read()
     m = re.search(r"struct TileArgs \{.*?\n\};", hdr, re.S)
@@ -394,13 +394,30 @@ def config_legs(api, W, device: int, cfg1_oracle):
     leg = {"workload": CFG1_WORKLOAD, "precision": "c128", "solve_s": sec, "steps_per_s": steps / sec,
            "krylov_iterations_per_step": st["krylov_iterations"] / steps, "kernel_launches": st["kernel_launches"],
            "krylov_error_estimate": st["max_error_estimate"]}
+    # the same solve as one persistent launch of the batched kernel (a batch of
+    # one register: every step and Krylov iteration on the device)
+    b = api.Batch(ctx, [prob], 10, "c128", obs_stride=1)
+    b.run()  # first run captures the graph
+    walls, devs = [], []
+    for _ in range(5):
+        t0 = time.perf_counter()
+        b.run()
+        walls.append(time.perf_counter() - t0)
+        devs.append(b.stats()["seconds"])
+    psi_b, occ_b = b.state(0), b.occupations(0)
+    b.close()
+    one = {"solve_s": statistics.median(walls), "device_s": statistics.median(devs),
+           "steps_per_s": steps / statistics.median(walls)}
     if cfg1_oracle is not None:
         ref, occ_ref, osec = cfg1_oracle
         leg["error_vs_oracle"] = {**state_errors(psi, ref),
                                   "max_abs_occupation_error": float(np.max(np.abs(occ - occ_ref)))}
+        one["error_vs_oracle"] = {**state_errors(psi_b, ref),
+                                  "max_abs_occupation_error": float(np.max(np.abs(occ_b - occ_ref)))}
         leg["oracle_solve_s"] = osec
     else:
         leg["error_vs_oracle"] = None
+    leg["batched_single_launch"] = one
     out["rabi_chain_n8"] = leg
 
     prob = W.adiabatic_sweep_lattice(4, 5)
@@ -422,6 +439,41 @@ def config_legs(api, W, device: int, cfg1_oracle):
     out["adiabatic_sweep_4x5"] = sweep
     ctx.close()
     return out
+
+
+PHI_WORKLOAD = ("the 28-atom random box with a laser phase: phi_i ~ U(-pi, pi) per atom, constant in time "
+                "(complex flip coefficients), c64, dt = 5 ns, m_max = 20; steady-state steps")
+
+
+def phi_leg(api, W, device: int, warm: int = TRANSIENT_STEPS, steps: int = 3):
+    """Steady-state Lanczos steps of the random box with phi != 0 (the flip
+    kernels' complex-coefficient variant), beside the phi = 0 headline."""
+    import torch
+    base = W.random_box(seed=3, n=N_ATOMS, t_ns=(warm + steps) * DT_NS)
+    rng = np.random.Generator(np.random.PCG64(33))
+    phi = np.repeat(rng.uniform(-math.pi, math.pi, N_ATOMS)[:, None], base.t_ns, axis=1)
+    prob = W.Problem(base.positions, base.c6, base.t_ns, base.omega, base.delta, phi)
+    ctx = api.Context(device)
+    s = api.Solver(ctx, prob, DT_NS, "c64", m_max=M_MAX, obs_stride=1)
+    s.step(warm)
+    it0 = s.stats()["krylov_iterations"]
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.set_profiling(True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    s.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    kt = s.kernel_times()
+    st = s.stats()
+    s.close()
+    ctx.close()
+    per = {k: round(kt[k]["ms"] / max(1, kt[k]["launches"]), 4) for k in ("pass_first", "pass_second", "combine")}
+    return {"workload": PHI_WORKLOAD, "steps_per_s": steps / (ms / 1e3), "ms_per_step": ms / steps,
+            "krylov_iterations_per_step": (st["krylov_iterations"] - it0) / steps,
+            "ms_per_launch": per, "krylov_error_estimate": st["max_error_estimate"]}
 
 
 def cfg1_oracle_baseline():
@@ -656,6 +708,7 @@ def ours(args):
     if rank == 0 and not args.no_cpu_baseline:
         cfg1_oracle = cfg1_oracle_baseline()
     configs = None if args.no_configs else config_legs(api, W, local, cfg1_oracle)
+    phi = None if args.no_configs else phi_leg(api, W, local)
     batched = None if args.no_batch else batched_leg(api, W, local)
     serving = None if args.serve_requests <= 0 else serving_leg(api, W, local, args.serve_requests,
                                                                 args.serve_max_atoms)
@@ -697,6 +750,7 @@ def ours(args):
             "clocks": clk,
             "cpu_baseline": cpu,
             "configs": configs,
+            "random_box_phi": phi,
             "batched": batched,
             "serving": serving,
             "gradient": gradient,

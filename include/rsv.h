@@ -109,6 +109,8 @@ typedef struct {
   int32_t l2_partner_bits;    /* strided pass: bits whose flip partners are read through L2 */
   int32_t tile_order_bits;    /* strided pass: segment-index bits varied fastest across tiles (autotuned) */
   int32_t krylov_dim_max;     /* Krylov dimension cap in use (m_max; autotuned for batches created with m_max < 0) */
+  int32_t strided_tile_bits;  /* strided pass: log2 amplitudes of its shared-memory tile (x-only tiles: 13 for
+                                 complex64, 12 for complex128; tiles staging x and z: 12 / 11); 0 = one pass */
 } rsv_stats;
 
 /* Kernel classes of the time step, for rsv_solver_kernel_times. */

@@ -16,6 +16,10 @@ constexpr int kConsumerWarps = 16;
 constexpr int kConsumers = kConsumerWarps * 32;
 constexpr int kTileThreads = kConsumers;       // warp 0 also issues the TMA loads
 constexpr int kStages = 3;                     // shared-memory ring depth (2 tiles per stage)
+// Strided pass with x alone staged (strided_kernels.cu): 64 KiB tiles.
+constexpr int kStridedTileBitsF = 13;          // complex64: 2^13 amplitudes
+constexpr int kStridedTileBitsD = 12;          // complex128: 2^12 amplitudes
+constexpr int kStridedStages = 3;
 
 struct TileArgs {
   int n;         // atoms = state bits
@@ -39,16 +43,21 @@ struct TileArgs {
   const KState* ks;
   double* partials;      // [grid][3]
   int* err;              // device error word: bit 0 = a bounded wait timed out
-  const double* diag;    // first pass: [num_tiles][kDiagStride] rows of w_q (q < L) and E_hi at [15]
+  const void* diag;      // first pass: [num_tiles][kDiagStride] diagonal half tables (working precision)
 };
 
-// Per-tile diagonal decomposition rows (diag_kernels.cu): for the contiguous
-// tile tau (amplitude bits >= L fixed to the bits of tau),
-//   row[q] = w_q = sum_{r >= L} V_qr tau_r - delta_q   (q < L)
-//   row[15] = E_hi = sum_{L <= q < r} V_qr tau_q tau_r - sum_{q >= L} delta_q tau_q
-constexpr int kDiagStride = 16;
-cudaError_t launch_diag_table(const StepParams* sp, const double* vmat, int n, int L, int64_t num_tiles, double* out,
-                              cudaStream_t stream);
+// Per-tile diagonal half tables (diag_kernels.cu). For the contiguous tile
+// tau (amplitude bits >= L fixed to the bits of tau), with
+//   w_q  = sum_{r >= L} V_qr tau_r - delta_q   (q < L)
+//   E_hi = sum_{L <= q < r} V_qr tau_q tau_r - sum_{q >= L} delta_q tau_q,
+// the row holds, computed in FP64 and rounded once to the working precision,
+//   row[i]      = sum_{q < 6} w_q i_q                       (i < 64)
+//   row[64 + i] = E_hi + sum_{6 <= q < L} w_q i_{q-6}      (i < 64)
+// so that E(b) = row[b mod 64] + row[64 + (b mod 2^L) / 64] + Q[b mod 2^L].
+constexpr int kDiagHalf = 64;
+constexpr int kDiagStride = 2 * kDiagHalf;
+cudaError_t launch_diag_table(const StepParams* sp, const double* vmat, int n, int L, int64_t num_tiles, void* out,
+                              bool c64, cudaStream_t stream);
 
 // Tensor maps of the strided pass's two input tiles.
 struct TileMaps {
@@ -66,6 +75,13 @@ enum class TileMode {
 
 cudaError_t launch_tile(const TileArgs& args, const TileMaps* maps, TileMode mode, bool c64, bool phi, int grid,
                         cudaStream_t stream);
+// The strided pass with x alone staged in shared memory (64 KiB tiles, z
+// prefetched into L2 and read/written by its owning threads): args.L must be
+// kStridedTileBitsF (complex64) or kStridedTileBitsD (complex128) with every
+// strided bit present (a + L - c <= n). lanczos: also reduce Re<x, z>, |z|^2,
+// |x|^2 into partials (kLanczosSecond); else a plain matvec second pass.
+cudaError_t launch_strided(const TileArgs& args, const TileMaps* maps, bool lanczos, bool c64, bool phi, int grid,
+                           cudaStream_t stream);
 // Tensor map over a state vector for the strided-pass tile geometry `g`.
 bool encode_tile_map(CUtensorMap* out, const void* base, const TileArgs& g, bool c64);
 

@@ -23,27 +23,40 @@ constexpr int kMaxPieces = 4096;
 // J_0 + 2 sum_k J_{2k} = 1. Long times are split into pieces with x <= kXMax.
 // Called by one full warp; w lives in shared memory (re, im arrays).
 // ---------------------------------------------------------------------------
+// Warp-collective: J[0..K] = J_k(x). The backward recurrence itself is serial
+// (lane 0) and multiplies by a hoisted 2/x instead of dividing (FP64 division
+// is a long dependent sequence on this part, and it sat inside the loop); the
+// normalisation sum and the scaling are spread over the warp.
 __device__ inline void bessel_miller(double x, int K, double* J) {
-  // J[0..K] = J_k(x); computed by lane 0.
-  int M = K + 20 + (int)(5.0 * cbrt(x));
+  const int lane = threadIdx.x & 31;
+  int M = K + 20 + (int)(5.0f * cbrtf((float)x));
   if (M > kMaxBessel - 2) M = kMaxBessel - 2;
-  double jp1 = 0.0, jk = 1e-280;
-  J[M] = jk;
-  for (int k = M; k >= 1; --k) {
-    const double jm1 = (2.0 * k / x) * jk - jp1;
-    J[k - 1] = jm1;
-    jp1 = jk;
-    jk = jm1;
-    if (fabs(jm1) > 1e250) {
-      for (int i = k - 1; i <= M; ++i) J[i] *= 1e-250;
-      jp1 *= 1e-250;
-      jk *= 1e-250;
+  if (lane == 0) {
+    const double two_over_x = 2.0 / x;
+    double jp1 = 0.0, jk = 1e-280;
+    J[M] = jk;
+    for (int k = M; k >= 1; --k) {
+      const double jm1 = fma((double)k * two_over_x, jk, -jp1);
+      J[k - 1] = jm1;
+      jp1 = jk;
+      jk = jm1;
+      if (fabs(jm1) > 1e250) {
+        for (int i = k - 1; i <= M; ++i) J[i] *= 1e-250;
+        jp1 *= 1e-250;
+        jk *= 1e-250;
+      }
     }
   }
-  double s = J[0];
-  for (int k = 2; k <= M; k += 2) s += 2.0 * J[k];
-  const double inv = 1.0 / s;
-  for (int k = 0; k <= K; ++k) J[k] *= inv;
+  __syncwarp();
+  // normalisation J_0 + 2 sum_k J_{2k} = 1, summed in a fixed order per lane
+  double s = 0.0;
+  for (int k = 2 + 2 * lane; k <= M; k += 64) s += J[k];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  const double inv = 1.0 / (J[0] + 2.0 * s);
+  __syncwarp();
+  for (int k = lane; k <= K; k += 32) J[k] *= inv;
+  __syncwarp();
 }
 
 struct ChebWork {
@@ -128,10 +141,10 @@ __device__ inline void cheb_expm_e1(const double* al, const double* be, int m, d
   int pieces = (int)ceil(xt / kXMax);
   if (pieces < 1) pieces = 1;
   const double tp = tau / pieces, x = tp * rad, irad = 1.0 / rad;
-  int K = (int)(x + 12.0 * cbrt(x) + 30.0);
+  int K = (int)(x + 12.0f * cbrtf((float)x) + 30.0f);
   if (K > kMaxBessel - 40) K = kMaxBessel - 40;
-  if (lane == 0) {
-    if (x < 1e-6) {
+  if (x < 1e-6) {
+    if (lane == 0) {
       // power series J_k(x) = (x/2)^k / k! (1 - (x/2)^2 / (k+1) + ...), k <= 3
       const double h = 0.5 * x;
       w.J[0] = 1.0 - h * h;
@@ -139,8 +152,10 @@ __device__ inline void cheb_expm_e1(const double* al, const double* be, int m, d
       w.J[2] = 0.5 * h * h;
       w.J[3] = h * h * h / 6.0;
       w.kmax = 3;
-    } else {
-      bessel_miller(x, K, w.J);
+    }
+  } else {
+    bessel_miller(x, K, w.J);
+    if (lane == 0) {
       int kmax = K;
       while (kmax > 1 && kmax > x && fabs(w.J[kmax]) < 1e-18) --kmax;
       w.kmax = kmax;
@@ -150,6 +165,56 @@ __device__ inline void cheb_expm_e1(const double* al, const double* be, int m, d
   const int kmax = w.kmax;
   double ps, pc;
   sincos(tp * cen, &ps, &pc);
+  if (m <= 32) {
+    // Register path, one component per lane: the three-term recurrence
+    // phi_{k+1} = 2 S phi_k - phi_{k-1} with 2 S's entries folded into three
+    // per-lane coefficients and the neighbours phi_k[i -+ 1] by shuffles, so a
+    // term costs 8 FP64 instructions (FP64 issues slowly on this part).
+    const int i = lane;
+    const bool act = i < m;
+    const double a2 = act ? 2.0 * (al[i] - cen) * irad : 0.0;
+    const double bl = (act && i > 0) ? 2.0 * be[i] * irad : 0.0;
+    const double br = (act && i + 1 < m) ? 2.0 * be[i + 1] * irad : 0.0;
+    double uR = act ? ur[i] : 0.0, uI = act ? ui[i] : 0.0;
+    for (int piece = 0; piece < pieces; ++piece) {
+      double pR = uR, pI = uI;  // phi_0
+      double aR = w.J[0] * pR, aI = w.J[0] * pI;
+      // phi_1 = S phi_0
+      double cR = 0.5 * fma(a2, pR, fma(bl, __shfl_up_sync(0xffffffffu, pR, 1), br * __shfl_down_sync(0xffffffffu, pR, 1)));
+      double cI = 0.5 * fma(a2, pI, fma(bl, __shfl_up_sync(0xffffffffu, pI, 1), br * __shfl_down_sync(0xffffffffu, pI, 1)));
+      {
+        const double c = 2.0 * w.J[1];  // (-i)^1
+        aR = fma(c, cI, aR);
+        aI = fma(-c, cR, aI);
+      }
+      for (int k = 2; k <= kmax; ++k) {
+        const double nR = fma(a2, cR, fma(bl, __shfl_up_sync(0xffffffffu, cR, 1),
+                                          fma(br, __shfl_down_sync(0xffffffffu, cR, 1), -pR)));
+        const double nI = fma(a2, cI, fma(bl, __shfl_up_sync(0xffffffffu, cI, 1),
+                                          fma(br, __shfl_down_sync(0xffffffffu, cI, 1), -pI)));
+        pR = cR;
+        pI = cI;
+        cR = nR;
+        cI = nI;
+        const double c = 2.0 * w.J[k];
+        switch (k & 3) {  // (-i)^k
+          case 0: aR = fma(c, nR, aR); aI = fma(c, nI, aI); break;
+          case 1: aR = fma(c, nI, aR); aI = fma(-c, nR, aI); break;
+          case 2: aR = fma(-c, nR, aR); aI = fma(-c, nI, aI); break;
+          default: aR = fma(-c, nI, aR); aI = fma(c, nR, aI); break;
+        }
+      }
+      // u = exp(-i tp cen) * acc
+      uR = pc * aR + ps * aI;
+      uI = pc * aI - ps * aR;
+    }
+    if (act) {
+      ur[i] = uR;
+      ui[i] = uI;
+    }
+    __syncwarp();
+    return;
+  }
   for (int piece = 0; piece < pieces; ++piece) {
     // phi_0 = u, phi_1 = S u
     for (int i = lane; i < m; i += 32) {

@@ -210,9 +210,18 @@ int first_pass_gbits() {
   return (v >= 0 && v <= 4) ? v : kFirstPassGBits;
 }
 
-Plan make_plan(int n, bool c64, int num_sms, int seg_bits = kMinSegmentBits, int f1_fast = 0) {
+// Strided-pass shape: segment bits c, tile-order bits f1_fast and the tile
+// kind (x-only 64 KiB tiles, or 32 KiB x and z tiles), packed into one int.
+constexpr int kShapeXOnly = 256;
+int pack_shape(int seg, int f1f, bool x_only) { return seg * 16 + f1f + (x_only ? kShapeXOnly : 0); }
+int shape_seg(int shape) { return (shape & 255) / 16; }
+int shape_f1(int shape) { return shape % 16; }
+bool shape_x_only(int shape) { return (shape & kShapeXOnly) != 0; }
+
+Plan make_plan(int n, bool c64, int num_sms, int seg_bits = kMinSegmentBits, int f1_fast = 0, bool x_only = false) {
   Plan p;
   const int lt = c64 ? kTileBitsC64 : kTileBitsC128;
+  const int lx = c64 ? kStridedTileBitsF : kStridedTileBitsD;
   const int v = c64 ? 1 : 0;
   auto geom = [&](TileArgs& t, int L, int c, int a, int nG) {
     t.n = n;
@@ -232,10 +241,15 @@ Plan make_plan(int n, bool c64, int num_sms, int seg_bits = kMinSegmentBits, int
   } else {
     const int ga = std::min(first_pass_gbits(), n - lt - 1);
     geom(p.a, lt, lt, lt, ga);
-    const int h = std::min(n - lt - ga, lt - seg_bits);
-    const int c = lt - h;
-    geom(p.b, lt, c, lt + ga, 0);
-    p.b.split_h = (lt - c) > 8;
+    if (x_only && n - lt - ga >= lx - seg_bits) {
+      // x-only 64 KiB tiles: all lx - c strided bits fit above the first pass's
+      geom(p.b, lx, seg_bits, lt + ga, 0);
+    } else {
+      const int h = std::min(n - lt - ga, lt - seg_bits);
+      const int c = lt - h;
+      geom(p.b, lt, c, lt + ga, 0);
+    }
+    p.b.split_h = (p.b.L - p.b.c) > 8;
     p.b.f1_fast = std::min(f1_fast, p.b.a - p.b.c);
     p.b.nG = p.b.nF2;  // callers check nG <= kMaxGBits
     p.two_pass = true;
@@ -381,26 +395,57 @@ int tile_order_override() {
   return (v >= 0 && v <= 8) ? v : 0;
 }
 
-// A strided-pass shape the kernels accept for this register.
-bool shape_valid(int n, bool c64, int num_sms, int seg, int f1f) {
-  const Plan p = make_plan(n, c64, num_sms, seg, f1f);
-  return !p.two_pass || (p.b.nG <= kMaxGBits && p.b.c >= (c64 ? 1 : 0));
+int x_only_override() {
+  const char* e = std::getenv("RSV_STRIDED_X_ONLY");
+  return e ? (std::atoi(e) != 0) : 0;
 }
 
-// The overridden shape (seg_bits * 16 + f1_fast), or 0 when none is set or
-// the one set does not fit this register.
+Plan plan_for(int n, bool c64, int num_sms, int shape) {
+  return make_plan(n, c64, num_sms, shape_seg(shape), shape_f1(shape), shape_x_only(shape));
+}
+
+// A strided-pass shape the kernels accept for this register (an x-only shape
+// must get its 64 KiB tile: make_plan falls back to the staged-z tile when
+// the register has too few high bits).
+bool shape_valid(int n, bool c64, int num_sms, int shape) {
+  const Plan p = plan_for(n, c64, num_sms, shape);
+  if (!p.two_pass) return true;
+  const int lx = c64 ? kStridedTileBitsF : kStridedTileBitsD;
+  if (shape_x_only(shape) && p.b.L != lx) return false;
+  return p.b.nG <= kMaxGBits && p.b.c >= (c64 ? 1 : 0);
+}
+
+// The overridden shape, or 0 when none is set or the one set does not fit
+// this register. RSV_STRIDED_X_ONLY=1 selects the x-only tiles.
 int shape_override(int n, bool c64, int num_sms) {
   const int o = segment_override();
   if (!o) return 0;
-  const int f = tile_order_override();
-  return shape_valid(n, c64, num_sms, o, f) ? o * 16 + f : 0;
+  const int shape = pack_shape(o, tile_order_override(), x_only_override());
+  return shape_valid(n, c64, num_sms, shape) ? shape : 0;
 }
 
-// Tuned shape packed as seg_bits * 16 + f1_fast.
+// Tuned shape (pack_shape) of this register size and precision.
 int shape_for(rsv_ctx* ctx, int n, bool c64) {
   if (const int o = shape_override(n, c64, ctx->num_sms)) return o;
   auto it = ctx->tuned_segment.find({n, c64 ? 1 : 0});
-  return it == ctx->tuned_segment.end() ? kMinSegmentBits * 16 : it->second;
+  return it == ctx->tuned_segment.end() ? pack_shape(kMinSegmentBits, 0, false) : it->second;
+}
+
+// Candidates the tuner times: staged-z tiles with c in {4, 5} x f1_fast in
+// {0, 2, 4}, and x-only tiles with c in {2, 3, 4, 5}, each with tile orders
+// that put the 256-byte run of its segments (and one step beyond) side by side.
+std::vector<int> tune_candidates() {
+  std::vector<int> out;
+  for (int seg : {4, 5})
+    for (int f1f : {0, 2, 4}) out.push_back(pack_shape(seg, f1f, false));
+  for (int seg : {2, 3, 4, 5}) {
+    const int run = std::max(0, 5 - seg);  // segments per 256 bytes of complex64
+    for (int f1f : {0, run, run + 1}) {
+      const int sh = pack_shape(seg, f1f, true);
+      if (std::find(out.begin(), out.end(), sh) == out.end()) out.push_back(sh);
+    }
+  }
+  return out;
 }
 
 int tune_shape(rsv_ctx* ctx, cudaStream_t stream, int n, bool c64, StepParams* sp, double* vmat, KState* ks, double* part, void* x,
@@ -409,15 +454,15 @@ int tune_shape(rsv_ctx* ctx, cudaStream_t stream, int n, bool c64, StepParams* s
   const auto key = std::make_pair(n, c64 ? 1 : 0);
   auto it = ctx->tuned_segment.find(key);
   if (it != ctx->tuned_segment.end()) return it->second;
-  int best = kMinSegmentBits * 16;
+  int best = pack_shape(kMinSegmentBits, 0, false);
   float best_ms = 1e30f;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  for (int cand = 0; cand < 6; ++cand) {
-    const int seg = cand < 3 ? 4 : 5, f1f = (cand % 3) * 2;
-    Plan p = make_plan(n, c64, ctx->num_sms, seg, f1f);
-    if (!p.two_pass || p.b.nG > kMaxGBits || p.b.c < (c64 ? 1 : 0)) continue;
+  for (int shape : tune_candidates()) {
+    if (!shape_valid(n, c64, ctx->num_sms, shape)) continue;
+    const Plan p = plan_for(n, c64, ctx->num_sms, shape);
+    if (!p.two_pass) continue;
     TileArgs b = p.b;
     b.sp = sp;
     b.vmat = vmat;
@@ -438,7 +483,7 @@ int tune_shape(rsv_ctx* ctx, cudaStream_t stream, int n, bool c64, StepParams* s
     cudaEventElapsedTime(&ms, e0, e1);
     if (ms < best_ms) {
       best_ms = ms;
-      best = seg * 16 + f1f;
+      best = shape;
     }
   }
   cudaEventDestroy(e0);
@@ -477,7 +522,7 @@ struct rsv_solver {
   StepParams* d_sp = nullptr;
   double* d_vmat = nullptr;
   void* d_qtab = nullptr;
-  double* d_diag = nullptr;  // per-tile diagonal rows of the current step
+  void* d_diag = nullptr;    // per-tile diagonal half tables of the current step
   void* d_psi = nullptr;
   void* d_u[2] = {nullptr, nullptr};
   std::vector<void*> basis;
@@ -705,7 +750,7 @@ struct rsv_solver {
   rsv_status evolve(int k, double tau) {
     RSV_TRY(begin(tau, 0, nullptr));
     RSV_TRY(launch(RSV_KERNEL_CONTROL, 0.0, [&] {
-      return launch_diag_table(d_sp + k, d_vmat, n, plan.a.L, plan.a.num_tiles, d_diag, stream);
+      return launch_diag_table(d_sp + k, d_vmat, n, plan.a.L, plan.a.num_tiles, d_diag, c64, stream);
     }));
     const int m_max = cfg.m_max;
     int restarts = 0;
@@ -806,7 +851,7 @@ struct rsv_hamiltonian {
   StepParams* d_sp = nullptr;
   double* d_vmat = nullptr;
   void* d_qtab = nullptr;
-  double* d_diag = nullptr;
+  void* d_diag = nullptr;
   KState* d_ks = nullptr;  // error word of the bounded waits
   double* d_part = nullptr;
   const void* map_x = nullptr;  // operands the cached tensor maps describe
@@ -900,7 +945,7 @@ size_t rsv_footprint_bytes(int32_t n_atoms, int32_t precision, int32_t m_max) {
   const size_t D = size_t(1) << n_atoms;
   const size_t vec = D * (size_t)amp_bytes(precision);
   const int L = precision == RSV_C64 ? kTileBitsC64 : kTileBitsC128;
-  const size_t diag = sizeof(double) * kDiagStride * (n_atoms > L ? size_t(1) << (n_atoms - L) : 1);
+  const size_t diag = (size_t)amp_bytes(precision) / 2 * kDiagStride * (n_atoms > L ? size_t(1) << (n_atoms - L) : 1);
   // state + m_max basis vectors + two work vectors + per-tile diagonal rows +
   // parameter tables, partial sums and allocation rounding
   return vec * (size_t)(m_max + 3) + diag + (size_t(2) << 20);
@@ -968,7 +1013,7 @@ rsv_status rsv_apply_hamiltonian(rsv_ctx* ctx, int32_t n_atoms, int32_t precisio
   sp.has_phi = has_phi;
   const std::vector<double> vb = to_bit_matrix(n, v_pairs);
   const int shape = shape_for(ctx, n, c64);
-  Plan plan = make_plan(n, c64, ctx->num_sms, shape / 16, shape % 16);
+  Plan plan = plan_for(n, c64, ctx->num_sms, shape);
   RSV_CUDA(cudaMemcpyAsync(ctx->d_sp, &sp, sizeof(sp), cudaMemcpyHostToDevice, ctx->stream));
   RSV_CUDA(cudaMemcpyAsync(ctx->d_vmat, vb.data(), vb.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
   std::vector<float> qf;
@@ -981,18 +1026,18 @@ rsv_status rsv_apply_hamiltonian(rsv_ctx* ctx, int32_t n_atoms, int32_t precisio
     RSV_CUDA(cudaMemcpyAsync(ctx->d_qtab, qd.data(), qd.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
   }
   RSV_CUDA(cudaMemsetAsync(err_ptr(ctx->d_ks), 0, sizeof(int), ctx->stream));
-  double* d_diag = nullptr;
-  RSV_TRY(ctx->arena.alloc(sizeof(double) * kDiagStride * plan.a.num_tiles, (void**)&d_diag));
+  void* d_diag = nullptr;
+  RSV_TRY(ctx->arena.alloc((c64 ? sizeof(float) : sizeof(double)) * kDiagStride * plan.a.num_tiles, &d_diag));
   struct DiagGuard {
     rsv_ctx* c;
-    double* p;
+    void* p;
     ~DiagGuard() {
       cudaStreamSynchronize(c->stream);
       c->arena.release(p);
     }
   } diag_guard{ctx, d_diag};
   {
-    cudaError_t e = launch_diag_table(ctx->d_sp, ctx->d_vmat, n, plan.a.L, plan.a.num_tiles, d_diag, ctx->stream);
+    cudaError_t e = launch_diag_table(ctx->d_sp, ctx->d_vmat, n, plan.a.L, plan.a.num_tiles, d_diag, c64, ctx->stream);
     if (e != cudaSuccess) return fail(RSV_ERR_CUDA, std::string("diag table: ") + cudaGetErrorString(e));
   }
   TileArgs a = plan.a;
@@ -1052,12 +1097,12 @@ rsv_status rsv_hamiltonian_create(rsv_ctx* ctx, int32_t n_atoms, int32_t precisi
   sp.has_phi = h->phi;
   const std::vector<double> vb = to_bit_matrix(n_atoms, v_pairs);
   const int shape = shape_for(ctx, n_atoms, h->c64);
-  h->plan = make_plan(n_atoms, h->c64, ctx->num_sms, shape / 16, shape % 16);
+  h->plan = plan_for(n_atoms, h->c64, ctx->num_sms, shape);
   if (h->plan.two_pass && h->plan.b.nG > kMaxGBits) return fail(RSV_ERR_INVALID_ARG, "n_atoms too large");
   RSV_TRY(h->alloc(sizeof(StepParams), (void**)&h->d_sp));
   RSV_TRY(h->alloc(sizeof(double) * kMaxAtoms * kMaxAtoms, (void**)&h->d_vmat));
   RSV_TRY(h->alloc((h->c64 ? sizeof(float) : sizeof(double)) << h->plan.L_a, &h->d_qtab));
-  RSV_TRY(h->alloc(sizeof(double) * kDiagStride * h->plan.a.num_tiles, (void**)&h->d_diag));
+  RSV_TRY(h->alloc((h->c64 ? sizeof(float) : sizeof(double)) * kDiagStride * h->plan.a.num_tiles, &h->d_diag));
   RSV_TRY(h->alloc(sizeof(KState), (void**)&h->d_ks));
   RSV_TRY(h->alloc(sizeof(double) * partials_doubles(ctx->num_sms), (void**)&h->d_part));
   RSV_CUDA(cudaMemcpyAsync(h->d_sp, &sp, sizeof(sp), cudaMemcpyHostToDevice, ctx->stream));
@@ -1072,7 +1117,8 @@ rsv_status rsv_hamiltonian_create(rsv_ctx* ctx, int32_t n_atoms, int32_t precisi
     RSV_CUDA(cudaStreamSynchronize(ctx->stream));
   }
   RSV_CUDA(cudaMemsetAsync(h->d_ks, 0, sizeof(KState), ctx->stream));
-  RSV_CUDA(launch_diag_table(h->d_sp, h->d_vmat, n_atoms, h->plan.a.L, h->plan.a.num_tiles, h->d_diag, ctx->stream));
+  RSV_CUDA(launch_diag_table(h->d_sp, h->d_vmat, n_atoms, h->plan.a.L, h->plan.a.num_tiles, h->d_diag, h->c64,
+                             ctx->stream));
   RSV_CUDA(cudaStreamSynchronize(ctx->stream));
   ctx->hamiltonians.insert(h.get());
   *out = h.release();
@@ -1353,7 +1399,7 @@ static rsv_status solver_create(rsv_ctx* ctx, const rsv_problem* problem, const 
   A(sizeof(StepParams) * s->nsteps, (void**)&s->d_sp);
   A(sizeof(double) * kMaxAtoms * kMaxAtoms, (void**)&s->d_vmat);
   A(amp_bytes(cfg.precision) / 2 * (size_t(1) << s->plan.L_a), &s->d_qtab);
-  A(sizeof(double) * kDiagStride * s->plan.a.num_tiles, (void**)&s->d_diag);
+  A((s->c64 ? sizeof(float) : sizeof(double)) * kDiagStride * s->plan.a.num_tiles, &s->d_diag);
   A(vbytes, &s->d_psi);
   A(vbytes, &s->d_u[0]);
   A(vbytes, &s->d_u[1]);
@@ -1375,7 +1421,7 @@ static rsv_status solver_create(rsv_ctx* ctx, const rsv_problem* problem, const 
   }
   if (s->plan.two_pass) {
     const int shape = tune_shape(ctx, s->stream, n, s->c64, s->d_sp, s->d_vmat, s->d_ks, s->d_part, s->basis[0], s->d_u[0]);
-    s->plan = make_plan(n, s->c64, ctx->num_sms, shape / 16, shape % 16);
+    s->plan = plan_for(n, s->c64, ctx->num_sms, shape);
     s->map_basis.resize(cfg.m_max);
     bool ok = true;
     for (int k = 0; k < cfg.m_max; ++k) ok = ok && encode_tile_map(&s->map_basis[k], s->basis[k], s->plan.b, s->c64);
@@ -1547,6 +1593,7 @@ rsv_status rsv_solver_stats(const rsv_solver* s, rsv_stats* out) {
   out->l2_partner_bits = s->plan.two_pass ? s->plan.b.nG : s->plan.a.nG;
   out->tile_order_bits = s->plan.two_pass ? s->plan.b.f1_fast : 0;
   out->krylov_dim_max = s->cfg.m_max;
+  out->strided_tile_bits = s->plan.two_pass ? s->plan.b.L : 0;
   return RSV_OK;
 }
 

@@ -66,8 +66,7 @@ __global__ void __launch_bounds__(kTileThreads, 1)
 
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ __align__(8) uint64_t full[kStages], empty[kStages], formed[kStages];
-  __shared__ Real s_w[kStages][kMaxAtoms];  // w_q of the staged tile (first pass), working precision
-  __shared__ Real s_ehi[kStages];
+  __shared__ Real s_t[kStages][kDiagStride];  // the staged tile's diagonal half tables (first pass)
   __shared__ Coef s_cp[kMaxAtoms][2];         // [amplitude bit][bit of the target], apply form
   __shared__ double s_red[3][kConsumerWarps];
 
@@ -141,12 +140,10 @@ __global__ void __launch_bounds__(kTileThreads, 1)
       }
     }
     if (FIRST) {
-      // this tile's diagonal decomposition row (c == L: tile bits are amplitude bits [0, L))
-      if (lane < kDiagStride) {
-        const double v = args.diag[tile * kDiagStride + lane];
-        if (lane < L) s_w[s][lane] = (Real)v;
-        if (lane == kDiagStride - 1) s_ehi[s] = (Real)v;
-      }
+      // this tile's diagonal half tables (c == L: tile bits are amplitude bits [0, L))
+      const Real* row = static_cast<const Real*>(args.diag) + tile * kDiagStride;
+#pragma unroll
+      for (int i = lane; i < kDiagStride; i += 32) s_t[s][i] = row[i];
       __syncwarp();
     }
     if (lane == 0) {
@@ -259,20 +256,16 @@ __global__ void __launch_bounds__(kTileThreads, 1)
           x[k] = k < keff ? lds_vec(T0, tvk[k]) : Vec{0ull, 0ull};
         }
         if (FIRST) {
-          Real sacc = s_ehi[s];
-#pragma unroll
-          for (int j = 0; j < KT; ++j)
-            if (j < kt && ((ct >> j) & 1)) sacc += s_w[s][V + j];
-          const Real lin = sacc;
+          // E(t) = T1[t mod 64] + T2[t / 64] + Q[t]: three terms, each rounded
+          // once from FP64, so the working-precision error is a few units of
+          // roundoff of |E| (a running sum over the tile bits would round at
+          // every bit)
 #pragma unroll
           for (int k = 0; k < K; ++k) {
-            Real lk = lin;
-#pragma unroll
-            for (int j = 0; j < KK; ++j)
-              if (j < kk && ((k >> j) & 1)) lk += s_w[s][V + kt + j];
             const int t = tvk[k] << V;
-            const Real e0 = lk + s_q[t];
-            const Real e1 = V == 1 ? lk + s_w[s][0] + s_q[t + 1] : e0;
+            const Real hi = s_t[s][kDiagHalf + (t >> 6)];
+            const Real e0 = (s_t[s][t & (kDiagHalf - 1)] + hi) + s_q[t];
+            const Real e1 = V == 1 ? (s_t[s][(t + 1) & (kDiagHalf - 1)] + hi) + s_q[t + 1] : e0;
             o[k] = scale2<Real>(x[k], e0, e1);
             if constexpr (C::kF) {
               // vector-lane bit: amplitude bit 0, the partner is the other half of the vector
@@ -439,6 +432,10 @@ static cudaError_t dispatch(const TileArgs& args, const TileMaps* maps, TileMode
 cudaError_t launch_tile(const TileArgs& args, const TileMaps* maps, TileMode mode, bool c64, bool phi, int grid,
                         cudaStream_t stream) {
   if (grid <= 0) return cudaErrorInvalidValue;
+  // a strided geometry of 64 KiB x-only tiles goes to the strided kernel
+  const bool second = mode == TileMode::kMatvecSecond || mode == TileMode::kLanczosSecond;
+  if (second && args.L == (c64 ? kStridedTileBitsF : kStridedTileBitsD))
+    return launch_strided(args, maps, mode == TileMode::kLanczosSecond, c64, phi, grid, stream);
   return c64 ? dispatch<float>(args, maps, mode, phi, grid, stream)
              : dispatch<double>(args, maps, mode, phi, grid, stream);
 }

@@ -239,22 +239,33 @@ def test_random_box_n24_one_step(ctx, random_box_n24_ref, prec):
     assert np.max(np.abs(occ - occ_ref)) <= OCC_TOL[prec]
 
 
-SHAPES = [(seg, f1) for seg in (4, 5) for f1 in (0, 2, 4)]
+# every strided-pass shape the autotuner times: (segment bits c, tile-order
+# bits, x-only 64 KiB tiles)
+SHAPES = [(seg, f1, 0) for seg in (4, 5) for f1 in (0, 2, 4)]
+SHAPES += [(seg, f1, 1) for seg in (2, 3, 4, 5) for f1 in sorted({0, max(0, 5 - seg), max(0, 5 - seg) + 1})]
 
 
-@pytest.mark.parametrize("seg,f1", SHAPES)
-def test_strided_shape_candidates(random_box_n24_ref, monkeypatch, seg, f1):
-    """Every strided-pass shape the autotuner may pick (segment bits c x tile
-    order bits), forced by the plan override instead of the tuner: one Lanczos
-    step at N = 24 in both precisions against the oracle, and sampled rows of
-    the 28-atom matvec through the prepared operator against hamiltonian_rows."""
+def force_shape(monkeypatch, seg, f1, x_only):
     monkeypatch.setenv("RSV_SEGMENT_BITS", str(seg))
     monkeypatch.setenv("RSV_TILE_ORDER_BITS", str(f1))
+    monkeypatch.setenv("RSV_STRIDED_X_ONLY", str(x_only))
+
+
+@pytest.mark.parametrize("seg,f1,x_only", SHAPES)
+def test_strided_shape_candidates(random_box_n24_ref, monkeypatch, seg, f1, x_only):
+    """Every strided-pass shape the autotuner may pick (segment bits c x tile
+    order bits x tile kind), forced by the plan override instead of the tuner:
+    one Lanczos step at N = 24 in both precisions against the oracle, and
+    sampled rows of the 28-atom matvec through the prepared operator against
+    hamiltonian_rows."""
+    force_shape(monkeypatch, seg, f1, x_only)
     c = api().Context(0)
     prob, psi0, ref, occ_ref = random_box_n24_ref
     for prec in ("c64", "c128"):
         psi, occ, st = gpu_evolve(c, prob, 5, prec, initial_state=psi0, m_max=40)
         assert st["segment_bits"] == seg and st["tile_order_bits"] == f1
+        tile = (13 if prec == "c64" else 12) if x_only else (12 if prec == "c64" else 11)
+        assert st["strided_tile_bits"] == tile
         assert O.infidelity(psi, ref) <= INFID_TOL[prec]
         assert np.max(np.abs(occ - occ_ref)) <= OCC_TOL[prec]
     n = 28
@@ -276,6 +287,38 @@ def test_strided_shape_candidates(random_box_n24_ref, monkeypatch, seg, f1):
     got = y[torch.tensor(idx, device="cuda")].cpu().numpy().astype(np.complex128)
     assert np.max(np.abs(got - want)) <= MATVEC_TOL["c64"] * scale_of(V, om, de) * np.max(np.abs(xs))
     del x, y
+    c.close()
+
+
+X_ONLY_MATVEC = [(n, prec, seg) for prec in ("c64", "c128") for n in (20, 21, 22) for seg in (2, 3, 4, 5)
+                 if n - (12 if prec == "c64" else 11) >= (13 if prec == "c64" else 12) - seg]
+
+
+@pytest.mark.parametrize("n,prec,seg", X_ONLY_MATVEC)
+@pytest.mark.parametrize("with_phi", [False, True])
+def test_x_only_strided_matvec(monkeypatch, n, prec, seg, with_phi):
+    """The x-only strided pass element by element against the oracle, at the
+    sizes where its 64 KiB tile just fits (no partner bit left for L2) and a
+    few bits beyond, through the prepared operator with the shape forced."""
+    force_shape(monkeypatch, seg, max(0, 5 - seg), 1)
+    c = api().Context(0)
+    rng = np.random.Generator(np.random.PCG64(2000 + n * 8 + seg))
+    side = 5.0 * math.ceil(math.sqrt(n)) + 5.0
+    pos = W.random_register(rng, n, side)
+    V = O.pair_interactions(pos, W.C6_DEFAULT)
+    om = rng.uniform(2.0, 9.0, n)
+    de = rng.normal(0.0, 3.0, n)
+    ph = rng.uniform(-math.pi, math.pi, n) if with_phi else np.zeros(n)
+    x = rand_state_gpu(n, prec, seed=7000 + n)
+    y = torch.empty_like(x)
+    h = api().Hamiltonian(c, n, prec, V, om, de, ph if with_phi else None)
+    h.apply(x, y)
+    h.sync()
+    h.close()
+    xh = x.cpu().numpy().astype(np.complex128)
+    ref = O.apply_hamiltonian(xh, V, om, de, ph)
+    err = np.max(np.abs(y.cpu().numpy().astype(np.complex128) - ref))
+    assert err <= MATVEC_TOL[prec] * scale_of(V, om, de) * np.max(np.abs(xh)), err
     c.close()
 
 
@@ -400,11 +443,15 @@ def test_n28_zero_drive_phases(ctx):
             a0 *= singles[i][occ[i]]
         ref = np.exp(-1j * e * T) * a0
         worst = max(worst, (abs(complex(psi[b]) - ref) - 1e-12) / abs(a0))
-    # E(b) is rounded once to FP32 (relative 6e-8 of up to ~1e4 rad/us, i.e. a
-    # phase error of ~1e-5 rad over 10 ns) and each of the 5 steps' Krylov
-    # exponentials is accurate to the tolerance 1e-7 plus FP32 rounding of
-    # its ~30 iterations; 2e-5 |a0| bounds the sum
-    assert worst <= 2e-5, worst
+    # The complex64 diagonal E(b) is three FP32 terms, each rounded once from
+    # FP64, summed in FP32, and multiplied into FP32 amplitudes: about 6 unit
+    # roundoffs (2^-24) of |E| <= sum_{i<j} V_ij + sum_i |delta_i|, i.e. a phase
+    # error of 6 * 2^-24 * |E|max * T (8 is used). The five Krylov steps add
+    # their tolerance (1e-7 per step, relative) and FP32 rounding of their
+    # iterations, covered by 1e-5.
+    e_max = float(np.sum(np.triu(V, 1)) + np.sum(np.abs(de)))
+    bound = 8 * 2.0 ** -24 * e_max * T + 1e-5
+    assert worst <= bound, (worst, bound)
 
 
 def test_n28_norm_conservation_random_box(ctx):

@@ -210,23 +210,23 @@ def test_unfreed_results_delay_admission(ctx):
     rng = np.random.Generator(np.random.PCG64(41))
     p1 = W.random_knot_problem(rng, 16, 60)
     p2 = W.random_knot_problem(rng, 16, 60)
-    need = A.request_bytes(p1, 10, "c128", m_max=4, obs_stride=0)
-    assert need == A.request_bytes(p2, 10, "c128", m_max=4, obs_stride=0)
+    need = A.request_bytes(p1, 10, "c128", m_max=12, obs_stride=0)
+    assert need == A.request_bytes(p2, 10, "c128", m_max=12, obs_stride=0)
     state = (2 ** 16) * 16
     srv = A.Server(ctx, slots=2, memory_bytes=need + state // 2, max_bypass_s=-1)
-    r1 = srv.poll(srv.submit(p1, 10, "c128", m_max=4, obs_stride=0))
+    r1 = srv.poll(srv.submit(p1, 10, "c128", m_max=12, obs_stride=0))
     q, running, held = srv.load()
     assert running == 0 and held == state
-    t2 = srv.submit(p2, 10, "c128", m_max=4, obs_stride=0)
+    t2 = srv.submit(p2, 10, "c128", m_max=12, obs_stride=0)
     assert srv.poll(t2, 300) is None  # waits behind the held state
     q, running, held = srv.load()
     assert q == 1 and running == 0
-    ref1 = A.run(ctx, p1, 10, "c128", m_max=4, obs_stride=0)
+    ref1 = A.run(ctx, p1, 10, "c128", m_max=12, obs_stride=0)
     assert np.array_equal(r1.state(), ref1.state())  # the held state is intact
     r1.close()
     r2 = srv.poll(t2, -1)
     assert r2 is not None
-    ref2 = A.run(ctx, p2, 10, "c128", m_max=4, obs_stride=0)
+    ref2 = A.run(ctx, p2, 10, "c128", m_max=12, obs_stride=0)
     assert np.array_equal(r2.state(), ref2.state())
     r2.close()
     assert srv.load()[2] == 0
