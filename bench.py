@@ -806,6 +806,37 @@ def profile_batch():
     return 0
 
 
+def profile_observables():
+    """The observation and sampling kernels at full size (28 atoms, complex64),
+    once each, for one-pass ncu DRAM captures: one steady-state Lanczos time
+    step of the random box (its combine writes psi and accumulates <n_i>),
+    rsv_observe, rsv_correlations (one masked observe pass per atom),
+    rsv_hamiltonian_expectation and rsv_sample (10^6 shots). The solver's
+    Krylov basis holds about 46 GB while the steps run."""
+    import torch
+    from paper_2510_09813_b300 import api
+    from paper_2510_09813_b300 import workloads as W
+    prob = W.random_box(seed=3, n=N_ATOMS, t_ns=6 * DT_NS)
+    ctx = api.Context(0)
+    s = api.Solver(ctx, prob, DT_NS, "c64", m_max=M_MAX, obs_stride=1)
+    s.run_to_end()
+    psi = torch.from_numpy(s.state()).cuda()
+    s.close()
+    n2, occ = api.observe(ctx, N_ATOMS, "c64", psi)
+    corr = api.correlations(ctx, N_ATOMS, "c64", psi)
+    V = api.pair_energies(prob.positions, prob.c6)
+    h = api.Hamiltonian(ctx, N_ATOMS, "c64", V, prob.omega[:, 0], prob.delta[:, 0], None)
+    e = h.expectation(psi)
+    h.close()
+    shots = api.sample(ctx, N_ATOMS, "c64", psi, 1_000_000, 7)
+    torch.cuda.synchronize()
+    ctx.close()
+    print(json.dumps({"profile_observables": N_ATOMS, "norm2": n2, "occ_sum": float(occ.sum()),
+                      "corr_trace": float(np.trace(corr)), "energy": [float(np.real(e[0])), float(e[1])],
+                      "shots": int(shots.size)}))
+    return 0
+
+
 def profile_legs():
     """The Lindblad and gradient legs alone, once each (ncu launch lists)."""
     from paper_2510_09813_b300 import api
@@ -834,11 +865,15 @@ def main():
                     help="run the small ncu case at N atoms instead of the benchmark")
     ap.add_argument("--profile-batch", action="store_true", help="run the small batched ncu case")
     ap.add_argument("--profile-legs", action="store_true", help="run only the Lindblad and gradient legs")
+    ap.add_argument("--profile-observables", action="store_true",
+                    help="run the observation and sampling kernels once each at 28 atoms")
     args = ap.parse_args()
     if args.profile_batch:
         return profile_batch()
     if args.profile_legs:
         return profile_legs()
+    if args.profile_observables:
+        return profile_observables()
     if args.profile_case:
         return profile_case(args.profile_case)
     if args.warmup < 3:

@@ -576,6 +576,7 @@ __global__ void __launch_bounds__(kThreads, 2) batch_kernel(const BatchArgs A) {
   Real* s_q = reinterpret_cast<Real*>(dyn + (2 * sizeof(Real) << TB));
   __shared__ Shared<Real> s;
   const int tid = threadIdx.x;
+  if (tid == 0) cheb_reset(s.cw);  // the kept expansion starts empty (first use is after barriers)
   Vec* states = reinterpret_cast<Vec*>(A.states);
   const int64_t wstride = A.work_stride >> V;
   Vec* work = reinterpret_cast<Vec*>(A.work) + (int64_t)blockIdx.x * wstride;

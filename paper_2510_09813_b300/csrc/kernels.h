@@ -86,8 +86,13 @@ cudaError_t launch_strided(const TileArgs& args, const TileMaps* maps, bool lanc
 bool encode_tile_map(CUtensorMap* out, const void* base, const TileArgs& g, bool c64);
 
 // Krylov control kernels (krylov_kernels.cu).
+struct ChebWork;
+// Bytes of the device buffer a solver keeps for the control kernel's reused
+// Chebyshev expansion (zero-filled before first use).
+size_t cheb_cache_bytes();
 struct ScalarArgs {
   KState* ks;
+  ChebWork* cache;    // device: the kept expansion, carried between launches
   const double* partials;
   int nparts;
   int m_max;

@@ -4,6 +4,7 @@
 // streaming path's scalar kernel and by the batched kernel.
 #pragma once
 
+#include "dword.cuh"
 #include "rsv_common.cuh"
 
 namespace rsv {
@@ -63,9 +64,20 @@ struct ChebWork {
   double pr[kMaxKrylov], pi[kMaxKrylov];  // phi_{k-1}
   double cr[kMaxKrylov], ci[kMaxKrylov];  // phi_k
   double ar[kMaxKrylov], ai[kMaxKrylov];  // accumulated sum
-  double J[kMaxBessel];
+  double J[kMaxBessel];                   // J_k(x), FP64
+  float jh[kMaxBessel], jl[kMaxBessel];   // (2 - delta_k0) J_k(x) as double words
   int kmax;
+  // The expansion (interval, pieces, Bessel factors, phase) is kept for reuse:
+  // it holds for every T_m whose Gershgorin interval lies in [c_lo, c_hi], at
+  // time c_tau. Successive Krylov dimensions of one step usually fit in the
+  // interval of the first, widened by a tenth, so Miller's recurrence (FP64,
+  // serial) runs about once per step rather than once per check.
+  int c_valid, c_pieces;
+  double c_lo, c_hi, c_tau, c_pc, c_ps;
 };
+
+// Forget the kept expansion (lane 0, before the first use of w).
+__device__ __forceinline__ void cheb_reset(ChebWork& w) { w.c_valid = 0; }
 
 // Apply S = (T - cen)/rad to (vr, vi) component i.
 __device__ __forceinline__ void apply_s(const double* al, const double* be, int m, double cen, double irad, int i,
@@ -96,7 +108,7 @@ __device__ __forceinline__ void acc_term(int k, double jk, double pr, double pi,
 
 // (ur, ui) <- exp(-i tau T_m) e_1.  al[0..m-1], be[1..m-1]; warp-collective.
 __device__ inline void cheb_expm_e1(const double* al, const double* be, int m, double tau, double* ur, double* ui,
-                             ChebWork& w) {
+                                    ChebWork& w) {
   const int lane = threadIdx.x & 31;
   double lo = 1e308, hi = -1e308;
   for (int i = lane; i < m; i += 32) {
@@ -110,107 +122,132 @@ __device__ inline void cheb_expm_e1(const double* al, const double* be, int m, d
     lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, off));
     hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, off));
   }
-  const double cen = 0.5 * (lo + hi), rad = 0.5 * (hi - lo);
   for (int i = lane; i < m; i += 32) {
     ur[i] = (i == 0) ? 1.0 : 0.0;
     ui[i] = 0.0;
   }
   __syncwarp();
-  if (!(rad > 1e-300) || m == 1) {
+  if (!(hi - lo > 2e-300) || m == 1) {
     if (lane == 0) {
       double s, c;
-      sincos(tau * cen, &s, &c);
+      sincos(tau * 0.5 * (lo + hi), &s, &c);
       ur[0] = c;
       ui[0] = -s;
     }
     __syncwarp();
     return;
   }
-  // |tau| * spectral radius beyond kMaxPieces pieces (or not finite) means the
-  // tridiagonal is not a physical one (corrupted recurrence): report NaN, which
-  // no acceptance test passes, instead of looping over an unbounded piece count
-  const double xt = tau * rad;
-  if (!(xt <= kXMax * kMaxPieces)) {
-    for (int i = lane; i < m; i += 32) {
-      ur[i] = __longlong_as_double(0x7ff8000000000000ll);
-      ui[i] = ur[i];
+  const bool hit = w.c_valid && w.c_tau == tau && w.c_lo <= lo && hi <= w.c_hi;
+  if (!hit) {
+    const double span = hi - lo;
+    const double lo2 = lo - 0.05 * span, hi2 = hi + 0.05 * span;
+    const double cen = 0.5 * (lo2 + hi2), rad = 0.5 * (hi2 - lo2);
+    // |tau| * spectral radius beyond kMaxPieces pieces (or not finite) means the
+    // tridiagonal is not a physical one (corrupted recurrence): report NaN, which
+    // no acceptance test passes, instead of looping over an unbounded piece count
+    const double xt = tau * rad;
+    if (!(xt <= kXMax * kMaxPieces)) {
+      for (int i = lane; i < m; i += 32) {
+        ur[i] = __longlong_as_double(0x7ff8000000000000ll);
+        ui[i] = ur[i];
+      }
+      __syncwarp();
+      return;
+    }
+    int pieces = (int)ceil(xt / kXMax);
+    if (pieces < 1) pieces = 1;
+    const double tp = tau / pieces, x = tp * rad;
+    int K = (int)(x + 12.0f * cbrtf((float)x) + 30.0f);
+    if (K > kMaxBessel - 40) K = kMaxBessel - 40;
+    if (x < 1e-6) {
+      if (lane == 0) {
+        // power series J_k(x) = (x/2)^k / k! (1 - (x/2)^2 / (k+1) + ...), k <= 3
+        const double h = 0.5 * x;
+        w.J[0] = 1.0 - h * h;
+        w.J[1] = h * (1.0 - 0.5 * h * h);
+        w.J[2] = 0.5 * h * h;
+        w.J[3] = h * h * h / 6.0;
+        w.kmax = 3;
+      }
+    } else {
+      bessel_miller(x, K, w.J);
+      if (lane == 0) {
+        int kmax = K;
+        while (kmax > 1 && kmax > x && fabs(w.J[kmax]) < 1e-18) --kmax;
+        w.kmax = kmax;
+      }
     }
     __syncwarp();
-    return;
-  }
-  int pieces = (int)ceil(xt / kXMax);
-  if (pieces < 1) pieces = 1;
-  const double tp = tau / pieces, x = tp * rad, irad = 1.0 / rad;
-  int K = (int)(x + 12.0f * cbrtf((float)x) + 30.0f);
-  if (K > kMaxBessel - 40) K = kMaxBessel - 40;
-  if (x < 1e-6) {
-    if (lane == 0) {
-      // power series J_k(x) = (x/2)^k / k! (1 - (x/2)^2 / (k+1) + ...), k <= 3
-      const double h = 0.5 * x;
-      w.J[0] = 1.0 - h * h;
-      w.J[1] = h * (1.0 - 0.5 * h * h);
-      w.J[2] = 0.5 * h * h;
-      w.J[3] = h * h * h / 6.0;
-      w.kmax = 3;
+    for (int k = lane; k <= w.kmax; k += 32) {
+      const DW c = dw_from(k == 0 ? w.J[0] : 2.0 * w.J[k]);
+      w.jh[k] = c.hi;
+      w.jl[k] = c.lo;
     }
-  } else {
-    bessel_miller(x, K, w.J);
     if (lane == 0) {
-      int kmax = K;
-      while (kmax > 1 && kmax > x && fabs(w.J[kmax]) < 1e-18) --kmax;
-      w.kmax = kmax;
+      double ps, pc;
+      sincos(tp * cen, &ps, &pc);
+      w.c_pc = pc;
+      w.c_ps = ps;
+      w.c_lo = lo2;
+      w.c_hi = hi2;
+      w.c_tau = tau;
+      w.c_pieces = pieces;
+      w.c_valid = 1;
     }
+    __syncwarp();
   }
-  __syncwarp();
-  const int kmax = w.kmax;
-  double ps, pc;
-  sincos(tp * cen, &ps, &pc);
+  const double cen = 0.5 * (w.c_lo + w.c_hi), irad = 1.0 / (0.5 * (w.c_hi - w.c_lo));
+  const int kmax = w.kmax, pieces = w.c_pieces;
+  const double pc = w.c_pc, ps = w.c_ps;
   if (m <= 32) {
-    // Register path, one component per lane: the three-term recurrence
-    // phi_{k+1} = 2 S phi_k - phi_{k-1} with 2 S's entries folded into three
-    // per-lane coefficients and the neighbours phi_k[i -+ 1] by shuffles, so a
-    // term costs 8 FP64 instructions (FP64 issues slowly on this part).
+    // Register path in double words, one component per lane: the three-term
+    // recurrence phi_{k+1} = 2 S phi_k - phi_{k-1} with 2 S's entries folded
+    // into three per-lane coefficients and the neighbours phi_k[i -+ 1] by
+    // shuffles. A term costs about 130 FP32 instructions, against 8 FP64 ones
+    // at some 70 cycles each.
     const int i = lane;
     const bool act = i < m;
-    const double a2 = act ? 2.0 * (al[i] - cen) * irad : 0.0;
-    const double bl = (act && i > 0) ? 2.0 * be[i] * irad : 0.0;
-    const double br = (act && i + 1 < m) ? 2.0 * be[i + 1] * irad : 0.0;
-    double uR = act ? ur[i] : 0.0, uI = act ? ui[i] : 0.0;
+    const DW a2 = dw_from(act ? 2.0 * (al[i] - cen) * irad : 0.0);
+    const DW bl = dw_from((act && i > 0) ? 2.0 * be[i] * irad : 0.0);
+    const DW br = dw_from((act && i + 1 < m) ? 2.0 * be[i + 1] * irad : 0.0);
+    const DW pcw = dw_from(pc), psw = dw_from(ps), zero{0.f, 0.f};
+    DW uR{i == 0 ? 1.f : 0.f, 0.f}, uI = zero;
     for (int piece = 0; piece < pieces; ++piece) {
-      double pR = uR, pI = uI;  // phi_0
-      double aR = w.J[0] * pR, aI = w.J[0] * pI;
-      // phi_1 = S phi_0
-      double cR = 0.5 * fma(a2, pR, fma(bl, __shfl_up_sync(0xffffffffu, pR, 1), br * __shfl_down_sync(0xffffffffu, pR, 1)));
-      double cI = 0.5 * fma(a2, pI, fma(bl, __shfl_up_sync(0xffffffffu, pI, 1), br * __shfl_down_sync(0xffffffffu, pI, 1)));
+      DW pR = uR, pI = uI;  // phi_0
+      const DW j0{w.jh[0], w.jl[0]};
+      DW aR = dw_axpy(zero, j0, pR), aI = dw_axpy(zero, j0, pI);
+      // phi_1 = S phi_0 = (2 S phi_0) / 2
+      DW cR = dw_stencil(a2, pR, bl, dw_shfl_up(pR, 1), br, dw_shfl_down(pR, 1), zero);
+      DW cI = dw_stencil(a2, pI, bl, dw_shfl_up(pI, 1), br, dw_shfl_down(pI, 1), zero);
+      cR = DW{0.5f * cR.hi, 0.5f * cR.lo};
+      cI = DW{0.5f * cI.hi, 0.5f * cI.lo};
       {
-        const double c = 2.0 * w.J[1];  // (-i)^1
-        aR = fma(c, cI, aR);
-        aI = fma(-c, cR, aI);
+        const DW c1{w.jh[1], w.jl[1]};  // (-i)^1
+        aR = dw_axpy(aR, c1, cI);
+        aI = dw_axpy(aI, dw_neg(c1), cR);
       }
       for (int k = 2; k <= kmax; ++k) {
-        const double nR = fma(a2, cR, fma(bl, __shfl_up_sync(0xffffffffu, cR, 1),
-                                          fma(br, __shfl_down_sync(0xffffffffu, cR, 1), -pR)));
-        const double nI = fma(a2, cI, fma(bl, __shfl_up_sync(0xffffffffu, cI, 1),
-                                          fma(br, __shfl_down_sync(0xffffffffu, cI, 1), -pI)));
+        const DW nR = dw_stencil(a2, cR, bl, dw_shfl_up(cR, 1), br, dw_shfl_down(cR, 1), pR);
+        const DW nI = dw_stencil(a2, cI, bl, dw_shfl_up(cI, 1), br, dw_shfl_down(cI, 1), pI);
         pR = cR;
         pI = cI;
         cR = nR;
         cI = nI;
-        const double c = 2.0 * w.J[k];
+        const DW ck{w.jh[k], w.jl[k]};
         switch (k & 3) {  // (-i)^k
-          case 0: aR = fma(c, nR, aR); aI = fma(c, nI, aI); break;
-          case 1: aR = fma(c, nI, aR); aI = fma(-c, nR, aI); break;
-          case 2: aR = fma(-c, nR, aR); aI = fma(-c, nI, aI); break;
-          default: aR = fma(-c, nI, aR); aI = fma(c, nR, aI); break;
+          case 0: aR = dw_axpy(aR, ck, nR); aI = dw_axpy(aI, ck, nI); break;
+          case 1: aR = dw_axpy(aR, ck, nI); aI = dw_axpy(aI, dw_neg(ck), nR); break;
+          case 2: aR = dw_axpy(aR, dw_neg(ck), nR); aI = dw_axpy(aI, dw_neg(ck), nI); break;
+          default: aR = dw_axpy(aR, dw_neg(ck), nI); aI = dw_axpy(aI, ck, nR); break;
         }
       }
       // u = exp(-i tp cen) * acc
-      uR = pc * aR + ps * aI;
-      uI = pc * aI - ps * aR;
+      uR = dw_stencil(pcw, aR, psw, aI, zero, zero, zero);
+      uI = dw_stencil(pcw, aI, dw_neg(psw), aR, zero, zero, zero);
     }
     if (act) {
-      ur[i] = uR;
-      ui[i] = uI;
+      ur[i] = dw_value(uR);
+      ui[i] = dw_value(uI);
     }
     __syncwarp();
     return;

@@ -47,7 +47,8 @@ struct KState {
   int64_t total_substeps;
   int32_t error;                 // set by kernels whose bounded waits timed out
   int32_t pad_i;
-  double pad_[6];
+  double tnorm;                  // Gershgorin bound of T_m so far (max row sum), reset per Krylov space
+  double pad_[5];
   // --- values consumed by the next "first" pass ---
   double form_a;                 // alpha_{j-1} (0 for j = 0)
   double form_s;                 // 1 / beta_j (1 / |psi| for j = 0)
@@ -59,7 +60,8 @@ struct KState {
   double coef_im[kMaxKrylov];
 };
 constexpr int kStatusBytes = 128;
-static_assert(sizeof(int32_t) * 6 + sizeof(double) * 5 + sizeof(int64_t) * 2 + sizeof(double) * 6 == kStatusBytes,
+static_assert(sizeof(int32_t) * 6 + sizeof(double) * 5 + sizeof(int64_t) * 2 + sizeof(double) * 1 +
+                  sizeof(double) * 5 == kStatusBytes,
               "status block layout");
 
 template <typename Real>

@@ -530,6 +530,7 @@ struct rsv_solver {
   std::vector<CUtensorMap> map_basis;  // strided-pass tensor maps over basis[j]
   CUtensorMap map_u[2];                // ... over the two work vectors
   KState* d_ks = nullptr;
+  ChebWork* d_cheb = nullptr;  // the control kernel's kept Chebyshev expansion
   double* d_part = nullptr;
   double* d_cpart = nullptr;
   double* d_occ = nullptr;   // [max_rows][n]
@@ -564,6 +565,7 @@ struct rsv_solver {
     }
     std::vector<char> zero_ks(sizeof(KState), 0);
     RSV_CUDA(cudaMemcpyAsync(d_ks, zero_ks.data(), sizeof(KState), cudaMemcpyHostToDevice, stream));
+    RSV_CUDA(cudaMemsetAsync(d_cheb, 0, cheb_cache_bytes(), stream));
     done = 0;
     rows = 0;
     last_m = 0;
@@ -596,6 +598,7 @@ struct rsv_solver {
     basis.clear();
     d_basis = nullptr;
     d_ks = nullptr;
+    d_cheb = nullptr;
     d_part = nullptr;
     d_cpart = nullptr;
     d_occ = nullptr;
@@ -758,6 +761,7 @@ struct rsv_solver {
       const int check_from = std::max(1, last_m - 2);
       ScalarArgs sa{};
       sa.ks = d_ks;
+      sa.cache = d_cheb;
       sa.partials = d_part;
       sa.nparts = plan.two_pass ? plan.grid_b : plan.grid_a;
       sa.m_max = m_max;
@@ -1407,6 +1411,7 @@ static rsv_status solver_create(rsv_ctx* ctx, const rsv_problem* problem, const 
   for (int k = 0; k < cfg.m_max; ++k) A(vbytes, &s->basis[k]);
   A(sizeof(void*) * cfg.m_max, (void**)&s->d_basis);
   A(sizeof(KState), (void**)&s->d_ks);
+  A(cheb_cache_bytes(), (void**)&s->d_cheb);
   A(sizeof(double) * partials_doubles(ctx->num_sms), (void**)&s->d_part);
   A(sizeof(double) * partials_doubles(ctx->num_sms), (void**)&s->d_cpart);
   A(sizeof(double) * n * s->max_rows, (void**)&s->d_occ);
