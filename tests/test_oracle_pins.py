@@ -407,6 +407,25 @@ def test_sweep_3x4_golden_matches_the_oracle():
     assert np.max(np.abs(np.asarray(occ_head) - occ[:12])) <= 1e-12
 
 
+def test_sweep_4x5_golden_matches_the_oracle():
+    """The stored 400-step evolution of the 20-atom 4x5 sweep (written with the
+    oracle's Chebyshev path) agrees with the oracle's Lanczos path, an
+    independent algorithm, on its first occupation rows; its final state is
+    normalised and has the lattice's mirror symmetry in the occupations."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "sweep_4x5_dt10.npz")
+    with np.load(path) as g:
+        psi, occ = g["psi"], g["occ"]
+    assert psi.shape == (2 ** 20,) and occ.shape == (401, 20)
+    assert abs(np.linalg.norm(psi) - 1.0) < 1e-12
+    # the 4x5 lattice is symmetric under the 180-degree rotation i -> 19 - i
+    assert np.max(np.abs(occ - occ[:, ::-1])) < 1e-10
+    prob = W.adiabatic_sweep_lattice(4, 5)
+    t_ns = 30
+    _, occ_head = O.evolve(prob.positions, prob.c6, t_ns, 10, prob.omega[:, :t_ns], prob.delta[:, :t_ns], None,
+                           method="krylov", tol=1e-14)
+    assert np.max(np.abs(np.asarray(occ_head) - occ[:4])) <= 1e-12
+
+
 def test_correlations_and_energy_moments():
     """Product states: <n_i n_j> = <n_i><n_j> for i != j and <n_i n_i> = <n_i>.
     A basis state at Omega = 0 is an eigenstate: <H> = E(b), variance 0. A
