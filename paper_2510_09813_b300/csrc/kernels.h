@@ -222,7 +222,8 @@ cudaError_t launch_multi_axpy(const void* const* V, const double* coef, int nvec
 // a barrier that nothing completes gives up.
 cudaError_t launch_wait_check(int* err, cudaStream_t stream);
 
-// Sampling (sample_kernels.cu)
+// Sampling (sample_kernels.cu): chunks of kSampleChunk amplitudes.
+constexpr int64_t kSampleChunk = 256;
 cudaError_t launch_block_sums(const void* psi, int64_t dim, bool c64, int64_t chunk, double* sums, cudaStream_t stream);
 cudaError_t launch_sample(const void* psi, int64_t dim, bool c64, int64_t chunk, const double* chunk_cdf, int64_t nchunks,
                           double total, int64_t shots, uint64_t seed, uint64_t* out, cudaStream_t stream);

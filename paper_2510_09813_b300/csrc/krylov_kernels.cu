@@ -4,167 +4,27 @@
 // in FP64; the convergence test; the Krylov combine psi' = |psi| sum_k u_k v_k;
 // and the observables <n_i> fused into the combine.
 #include "kernels.h"
+#include "krylov_control.cuh"
 #include "krylov_math.cuh"
 #include "rsv_common.cuh"
 
 namespace rsv {
 
 // ---------------------------------------------------------------------------
-// Scalar kernel: after the last streaming pass of Krylov iteration j.
-//
-// One CTA of four warps, one per SM sub-partition: FP64 instructions occupy a
-// sub-partition's FP64 unit for about 70 cycles each and do not pipeline
-// within a warp, so the launch keeps their count on the critical path small.
-// Every load the launch needs is issued first; the norm bound of T_m is kept
-// in the state (one row added per iteration); the tridiagonal and the kept
-// Chebyshev expansion are read only when the convergence test runs.
+// Scalar kernel: the Krylov control step of iteration j as a launch of its own
+// (krylov_control.cuh). The streaming solver normally runs the same step in the
+// last CTA of the iteration's last pass instead.
 // ---------------------------------------------------------------------------
-constexpr int kScalarThreads = 128;
-
-__global__ void __launch_bounds__(kScalarThreads, 1) scalar_kernel(const ScalarArgs A) {
-  __shared__ double s_part[3][kScalarThreads / 32];
-  __shared__ double s_al[kMaxKrylov], s_be[kMaxKrylov + 1];
-  __shared__ double s_ur[kMaxKrylov], s_ui[kMaxKrylov];
-  __shared__ ChebWork s_w;
-  KState* ks = A.ks;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  // ---- loads, all issued before any of them is used ----
-  const int status0 = ks->status;
-  const int j = ks->j;
-  double v[3] = {0.0, 0.0, 0.0};
-  for (int p = tid; p < A.nparts; p += kScalarThreads) {
-#pragma unroll
-    for (int i = 0; i < 3; ++i) v[i] += A.partials[(int64_t)p * 3 + i];
-  }
-  const int m = j + 1;
-  const bool maybe_check = m >= A.check_from || m >= A.m_max;
-  double tn_prev = 0.0, beta_j = 0.0, tau_rem = 0.0, b0 = 0.0;
-  double al_i = 0.0, al_i2 = 0.0, be_i = 0.0;  // rows of T_m by lane (and lane + 32)
-  if (warp == 0) {
-    tn_prev = ks->tnorm;
-    beta_j = j > 0 ? ks->beta[j] : 0.0;  // beta[0] is |psi|, not an entry of T
-    tau_rem = ks->tau_rem;
-    b0 = ks->beta[0];
-    if (maybe_check) {
-      if (lane < j) al_i = ks->alpha[lane];
-      if (lane <= j) be_i = ks->beta[lane];
-      if (lane + 32 < j) al_i2 = ks->alpha[lane + 32];
-    }
-  }
-  if (status0 != kContinue) return;  // uniform: the Krylov space is already accepted
-  // ---- partial sums: per warp, then four rows ----
-#pragma unroll
-  for (int i = 0; i < 3; ++i) {
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) v[i] += __shfl_xor_sync(0xffffffffu, v[i], off);
-  }
-  if (lane == 0) {
-#pragma unroll
-    for (int i = 0; i < 3; ++i) s_part[i][warp] = v[i];
-  }
-  __syncthreads();
-  if (warp != 0) return;
-  double rs = 0.0;  // lane i < 3: sum i
-  if (lane < 3)
-    for (int w = 0; w < kScalarThreads / 32; ++w) rs += s_part[lane][w];
-  const double r0 = __shfl_sync(0xffffffffu, rs, 0), r1 = __shfl_sync(0xffffffffu, rs, 1),
-               r2 = __shfl_sync(0xffffffffu, rs, 2);
-  // alpha_j = Re<v_j, u_j> / |v_j|^2 and beta_{j+1} = |u_j - alpha_j v_j| expanded
-  // as |u|^2 - 2 alpha Re<v,u> + alpha^2 |v|^2 = |u|^2 - alpha Re<v,u>.
-  const LanczosScalars ls = lanczos_scalars(r0, r1, r2);
-  const double alpha = ls.alpha, beta = ls.beta;
-  const int mk = ls.vanished ? m - 1 : m;  // accepted dimension if this space ends here
-  // Gershgorin bound of T_mk: the previous rows' maximum and row j
-  const double tn = ls.vanished ? tn_prev : fmax(tn_prev, fabs(alpha) + fabs(beta_j) + fabs(beta));
-  const bool breakdown = ls.vanished || beta <= A.breakdown * fmax(tn, 1e-300);
-  const bool check = breakdown || maybe_check;
-  KrylovDecision d{kContinue, 0.0, 0.0};
-  if (check) {
-    if (!maybe_check) {  // a breakdown before the expected dimension: load now
-      if (lane < j) al_i = ks->alpha[lane];
-      if (lane <= j) be_i = ks->beta[lane];
-      if (lane + 32 < j) al_i2 = ks->alpha[lane + 32];
-    }
-    if (lane < m) s_al[lane] = (lane == j) ? alpha : al_i;
-    if (lane + 32 < m) s_al[lane + 32] = (lane + 32 == j) ? alpha : al_i2;
-    for (int i = lane; i <= m; i += 32) s_be[i] = (i == m) ? beta : (i <= j && i < 32 ? be_i : ks->beta[i]);
-    // the kept expansion comes from the previous launch (global) and goes back
-    // after use; only its header and the Bessel factors matter
-    if (lane == 0) {
-      s_w.c_valid = A.cache->c_valid;
-      s_w.c_pieces = A.cache->c_pieces;
-      s_w.kmax = A.cache->kmax;
-      s_w.c_lo = A.cache->c_lo;
-      s_w.c_hi = A.cache->c_hi;
-      s_w.c_tau = A.cache->c_tau;
-      s_w.c_pc = A.cache->c_pc;
-      s_w.c_ps = A.cache->c_ps;
-    }
-    __syncwarp();
-    if (s_w.c_valid) {
-      for (int k = lane; k <= s_w.kmax; k += 32) {
-        s_w.J[k] = A.cache->J[k];
-        s_w.jh[k] = A.cache->jh[k];
-        s_w.jl[k] = A.cache->jl[k];
-      }
-    }
-    __syncwarp();
-    d = krylov_decide(s_al, s_be, mk, ls.vanished ? 0.0 : beta, tau_rem, breakdown, true, A.m_max, A.tol, s_ur,
-                      s_ui, s_w);
-    if (s_w.c_valid) {
-      for (int k = lane; k <= s_w.kmax; k += 32) {
-        A.cache->J[k] = s_w.J[k];
-        A.cache->jh[k] = s_w.jh[k];
-        A.cache->jl[k] = s_w.jl[k];
-      }
-      if (lane == 0) {
-        A.cache->c_pieces = s_w.c_pieces;
-        A.cache->kmax = s_w.kmax;
-        A.cache->c_lo = s_w.c_lo;
-        A.cache->c_hi = s_w.c_hi;
-        A.cache->c_tau = s_w.c_tau;
-        A.cache->c_pc = s_w.c_pc;
-        A.cache->c_ps = s_w.c_ps;
-        A.cache->c_valid = 1;
-      }
-    }
-  }
-  const int status = d.status;
-  const double tau_take = d.tau_take, err = d.err;
-  if (lane == 0) {
-    ks->alpha[j] = alpha;
-    ks->beta[m] = beta;
-    ks->tnorm = tn;
-    ks->total_iterations += 1;
-  }
-  if (status != kContinue) {
-    for (int i = lane; i < mk; i += 32) {
-      ks->coef_re[i] = b0 * s_ur[i];
-      ks->coef_im[i] = b0 * s_ui[i];
-    }
-    if (lane == 0) {
-      double rem = tau_rem - tau_take;
-      if (status == kDone || rem <= 1e-14 * tau_rem) rem = 0.0;
-      ks->m = mk;
-      ks->tau_taken = tau_take;
-      ks->tau_rem = rem;
-      ks->err_est = err;
-      ks->max_err_est = fmax(ks->max_err_est, err);
-      ks->status = status;
-    }
-  } else if (lane == 0) {
-    ks->form_a = alpha;
-    ks->form_s = 1.0 / beta;
-    ks->beta_prev = beta;
-    ks->j = j + 1;
-  }
+__global__ void __launch_bounds__(kControlThreads, 1) scalar_kernel(const ScalarArgs A) {
+  __shared__ ControlSmem w;
+  krylov_control(A, w);
 }
 
 size_t cheb_cache_bytes() { return sizeof(ChebWork); }
 
 cudaError_t launch_scalar(const ScalarArgs& a, cudaStream_t stream) {
   if (!a.cache) return cudaErrorInvalidValue;
-  scalar_kernel<<<1, kScalarThreads, 0, stream>>>(a);
+  scalar_kernel<<<1, kControlThreads, 0, stream>>>(a);
   return cudaGetLastError();
 }
 
@@ -271,12 +131,20 @@ __global__ void __launch_bounds__(kThreads) combine_kernel(const CombineArgs A) 
   // compensated; the per-thread accumulators stay in registers (compile-time
   // indices), the chunk-index bits use per-warp shared accumulators.
   Acc tot, lane_acc, reg_acc[KKMAX];
+  constexpr int kObserveBatch = 8;  // observe mode: vectors loaded ahead of their use
   for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
     Acc ct;
+    vec pre[kObserveBatch];  // observe mode: the next kObserveBatch vectors of the chunk
 #pragma unroll
     for (int k = 0; k < (1 << KKMAX); ++k) {
       if (k >= K || !active) continue;
       const int64_t vidx = ((ch << T) >> V) + (tid | (k << kt));
+      if (!A.combine && (k % kObserveBatch) == 0) {
+        // one batch of independent loads instead of one round trip per vector
+#pragma unroll
+        for (int u = 0; u < kObserveBatch; ++u)
+          if (k + u < K) pre[u] = __ldcs(reinterpret_cast<const vec*>(A.psi) + ((ch << T) >> V) + (tid | ((k + u) << kt)));
+      }
       Real x[R];
       if (A.combine) {
 #pragma unroll
@@ -307,7 +175,7 @@ __global__ void __launch_bounds__(kThreads) combine_kernel(const CombineArgs A) 
         }
         reinterpret_cast<vec*>(A.psi)[vidx] = *reinterpret_cast<const vec*>(x);
       } else {
-        *reinterpret_cast<vec*>(x) = reinterpret_cast<const vec*>(A.psi)[vidx];
+        *reinterpret_cast<vec*>(x) = pre[k % kObserveBatch];
         if (A.mask_bit >= 0) {
           // restrict to amplitudes whose bit mask_bit is 1
 #pragma unroll

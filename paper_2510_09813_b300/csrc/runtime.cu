@@ -1315,7 +1315,7 @@ rsv_status rsv_sample(rsv_ctx* ctx, int32_t n_atoms, int32_t precision, const vo
   cudaSetDevice(ctx->device);
   const bool c64 = precision == RSV_C64;
   const int64_t dim = int64_t(1) << n_atoms;
-  const int64_t chunk = std::min<int64_t>(dim, 4096);
+  const int64_t chunk = std::min<int64_t>(dim, kSampleChunk);
   const int64_t nchunks = (dim + chunk - 1) / chunk;
   double* d_sums = nullptr;
   uint64_t* d_out = nullptr;
