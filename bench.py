@@ -141,15 +141,18 @@ def replica_throughput(units_per_rank: float, seconds_max: float, world: int) ->
 
 
 def kernel_source_hash():
-    """Hash of the streaming-pass kernel's sources: its file, the device headers
-    it includes, and its argument struct."""
+    """Hash of the streaming-pass kernels' sources: their files, the device
+    headers they include (the fused control step's among them), and their
+    argument structs."""
     csrc = os.path.join(ROOT, "paper_2510_09813_b300", "csrc")
     h = hashlib.sha256()
-    for f in ("tile_kernels.cu", "strided_kernels.cu", "vec_ops.cuh", "tma.cuh", "rsv_common.cuh"):
+    for f in ("tile_kernels.cu", "strided_kernels.cu", "vec_ops.cuh", "tma.cuh", "rsv_common.cuh",
+              "krylov_control.cuh", "krylov_math.cuh", "dword.cuh"):
         h.update(open(os.path.join(csrc, f), "rb").read())
     hdr = open(os.path.join(csrc, "kernels.h")).read()
-    m = re.search(r"struct TileArgs \{.*?\n\};", hdr, re.S)
-    h.update((m.group(0) if m else hdr).encode())
+    for struct in ("ScalarArgs", "TileArgs"):
+        m = re.search(r"struct " + struct + r" \{.*?\n\};", hdr, re.S)
+        h.update((m.group(0) if m else hdr).encode())
     return h.hexdigest()[:16]
 
 
@@ -281,8 +284,12 @@ def batched_leg(api, W, device: int):
         b.run()
         secs.append(b.stats()["seconds"])
     st = b.stats()
+    # Krylov-iteration bytes of the last run, 24 B per amplitude of each
+    # register's vector (the streaming solver's unit), over its time
+    it_bytes = sum(b.stats(i)["krylov_iterations"] * 24.0 * 2 ** p.positions.shape[0] for i, p in enumerate(probs))
     b.close()
     sec = statistics.median(secs)
+    hbm, _ = peaks()
     sample = list(range(0, len(probs), 32))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -295,6 +302,8 @@ def batched_leg(api, W, device: int):
             "solves_per_s": len(probs) / sec,
             "seconds": sec, "steps_per_s": st["steps"] / sec, "krylov_iterations_per_s": st["krylov_iterations"] / sec,
             "resident_ctas": st["tile_passes"],
+            "krylov_iteration_GBps": round(it_bytes / secs[-1] / 1e9, 1),
+            "krylov_iteration_frac_of_hbm": round(it_bytes / secs[-1] / 1e9 / hbm, 4),
             "one_at_a_time_c128": {"solves_per_s": len(probs) / one_s,
                                    "sample": f"{len(sample)} of the {len(probs)} registers solved one by one "
                                              f"(rsv_run, complex128), scaled to all"},
@@ -478,6 +487,53 @@ def phi_leg(api, W, device: int, warm: int = TRANSIENT_STEPS, steps: int = 3):
             "ms_per_launch": per, "krylov_error_estimate": st["max_error_estimate"]}
 
 
+def control_leg(api, ctx, prob, start_state, fused_kt, fused_step_ms, steps: int = 3):
+    """The Krylov control step (reduce alpha_j and beta_{j+1}, test the space)
+    runs in the last CTA of each iteration's second pass; against the same
+    steady-state steps with the step as a launch of its own after the pass
+    (RSV_FLAG_CONTROL_LAUNCH): the step's device time either way (globaltimer,
+    split into steps that evaluate the small exponential and the rest), the
+    stand-alone kernel's event-timed duration, the second pass's duration both
+    ways, and whole-step times (the launch and its dependency gap saved)."""
+    import torch
+    stream = torch.cuda.current_stream()
+    s = api.Solver(ctx, prob, DT_NS, "c64", m_max=M_MAX, obs_stride=1, initial_state=start_state,
+                   control_launch=True)
+    s.step(2)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    s.set_profiling(True)  # as in the headline's timed steps
+    e0.record(stream)
+    s.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    step_ms = e0.elapsed_time(e1) / steps
+    kt = s.kernel_times()
+    s.close()
+
+    def per(d):
+        return d["ms"] / d["launches"] if d["launches"] else None
+
+    def device(c):
+        # device-timed control steps: all, those that evaluated the small
+        # exponential, and the rest
+        plain = c["steps"] - c["checks"]
+        return {"us_per_step": round(1e3 * c["ms"] / max(1, c["steps"]), 2), "steps": c["steps"],
+                "us_per_check": round(1e3 * c["check_ms"] / max(1, c["checks"]), 2), "checks": c["checks"],
+                "us_per_other": round(1e3 * (c["ms"] - c["check_ms"]) / max(1, plain), 2)}
+
+    return {"mode": "fused into the last CTA of the second pass",
+            "fused": {"device": device(fused_kt["control_step"]),
+                      "pass_second_ms_per_launch": round(per(fused_kt["pass_second"]), 4),
+                      "control_launches": fused_kt["control"]["launches"], "step_ms": round(fused_step_ms, 3)},
+            "separate_launch": {"device": device(kt["control_step"]),
+                                "control_us_per_launch": round(1e3 * per(kt["control"]), 2),
+                                "control_launches": kt["control"]["launches"],
+                                "pass_second_ms_per_launch": round(per(kt["pass_second"]), 4),
+                                "step_ms": round(step_ms, 3)},
+            "steps": steps}
+
+
 def cfg1_oracle_baseline():
     """The oracle's dense solve of the Rabi chain (cfg1), timed on the host:
     the CPU baseline of that configuration and the FP64 reference of its
@@ -580,7 +636,8 @@ def ours(args):
     start_state = solver.state()  # host copy for the end-to-end leg (untimed)
     it0 = solver.stats()["krylov_iterations"]
     l0 = solver.stats()["kernel_launches"]
-    kt = {k: {"ms": 0.0, "launches": 0, "bytes": 0.0} for k in ("pass_first", "pass_second", "control", "combine")}
+    kt = {k: {"ms": 0.0, "launches": 0, "bytes": 0.0} for k in ("pass_first", "pass_second", "control", "combine", "setup")}
+    kt["control_step"] = {}
     clocks = ClockSampler(local)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier()
@@ -606,8 +663,8 @@ def ours(args):
         torch.cuda.synchronize()
         ms += ev0.elapsed_time(ev1)
         for name, d in solver.kernel_times().items():
-            for f in ("ms", "launches", "bytes"):
-                kt[name][f] += d[f]
+            for f in d:
+                kt[name][f] = kt[name].get(f, 0) + d[f]
         solver.set_profiling(False)
         remaining -= k
     clk = clocks.stop()
@@ -629,20 +686,20 @@ def ours(args):
     hbm, src = peaks()
     amps = 2 ** N_ATOMS
     pass_bpa = {"pass_first": 32, "pass_second": 24}
-    per_ms = {k: kt[k]["ms"] / max(1, kt[k]["launches"]) for k in kt}
+    per_ms = {k: kt[k]["ms"] / max(1, kt[k]["launches"]) for k in kt if k != "control_step"}
     it_ms = per_ms["pass_first"] + per_ms["pass_second"]
     it_bytes = 24 * amps
     achieved = it_bytes / (it_ms / 1e3) / 1e9
     tr_a, tr_b = profiled_traffic("pass_first"), profiled_traffic("pass_second")
     traffic = None if tr_a is None or tr_b is None else (tr_a + tr_b) * amps
     kernels = {}
-    for k in ("pass_first", "pass_second", "combine", "control"):
+    for k in ("pass_first", "pass_second", "combine", "control", "setup"):
         d = kt[k]
         if d["launches"]:
             kernels[k] = {"launches": d["launches"], "ms_total": round(d["ms"], 3),
                           "ms_per_launch": round(d["ms"] / d["launches"], 4),
                           "algo_GBps": round(d["bytes"] / (d["ms"] / 1e3) / 1e9, 1) if d["ms"] > 0 else None}
-            if d["ms"] > 0 and k != "control":
+            if d["ms"] > 0 and k not in ("control", "setup"):
                 kernels[k]["frac_of_peak"] = round(d["bytes"] / (d["ms"] / 1e3) / 1e9 / hbm, 4)
             if k in pass_bpa:
                 kernels[k]["bytes_per_amp"] = pass_bpa[k]
@@ -706,6 +763,8 @@ def ours(args):
     res.close()
     ctx2.close()
 
+    control = control_leg(api, ctx, prob, start_state, kt, ms / args.steps)
+
     cfg1_oracle = None
     if rank == 0 and not args.no_cpu_baseline:
         cfg1_oracle = cfg1_oracle_baseline()
@@ -740,6 +799,7 @@ def ours(args):
             "krylov_iterations_per_s": ws * iters / (ms / 1e3),
             "roofline": roofline,
             "kernels": kernels,
+            "control": control,
             "tile_shape": {"passes": st["tile_passes"], "segment_bits": st["segment_bits"],
                            "l2_partner_bits": st["l2_partner_bits"], "tile_order_bits": st["tile_order_bits"]},
             "matvec": {"ms": round(mv_ms, 4), "algo_GBps": round(mv_gbs, 1), "frac_of_peak": round(mv_gbs / hbm, 4),

@@ -57,6 +57,12 @@ typedef int32_t rsv_status;
 #define RSV_C128 0
 #define RSV_C64 1
 
+/* rsv_config.flags */
+#define RSV_FLAG_CONTROL_LAUNCH 1 /* run each Krylov control step (the reduction of alpha_j and
+                                     beta_{j+1} and the convergence test of Sec. III.A.1) as a launch of
+                                     its own after the iteration's last pass, instead of in the last CTA
+                                     to finish that pass; same arithmetic and results, one more launch */
+
 typedef struct rsv_ctx rsv_ctx;
 typedef struct rsv_solver rsv_solver;
 typedef struct rsv_result rsv_result;
@@ -94,7 +100,7 @@ typedef struct {
                            convergence the step is split (Krylov restart on a shorter time) */
   int32_t max_substeps; /* restarts allowed per time step before RSV_ERR_NOT_CONVERGED; default 64 */
   int32_t obs_stride;   /* record <n_i> every obs_stride steps; 0 records only t = 0 and the end */
-  int32_t reserved;     /* must be 0 */
+  int32_t flags;        /* 0 or RSV_FLAG_CONTROL_LAUNCH; other bits: RSV_ERR_INVALID_ARG */
 } rsv_config;
 
 typedef struct {
@@ -116,14 +122,24 @@ typedef struct {
 /* Kernel classes of the time step, for rsv_solver_kernel_times. */
 #define RSV_KERNEL_PASS_FIRST 0  /* contiguous-tile pass: diagonal + low flips (+ the whole matvec if N is small) */
 #define RSV_KERNEL_PASS_SECOND 1 /* strided-tile pass: high flips + Lanczos reductions */
-#define RSV_KERNEL_CONTROL 2     /* Krylov scalar / restart kernels (one block each) */
+#define RSV_KERNEL_CONTROL 2     /* Krylov control step as a launch of its own (RSV_FLAG_CONTROL_LAUNCH;
+                                    fused into the second pass otherwise) */
 #define RSV_KERNEL_COMBINE 3     /* psi = |psi| sum_k u_k v_k fused with <n_i> */
-#define RSV_KERNEL_KINDS 4
+#define RSV_KERNEL_SETUP 4       /* per step and restart: diagonal tables, Krylov restart (begin) */
+#define RSV_KERNEL_KINDS 5
 
 typedef struct {
   double ms[RSV_KERNEL_KINDS];        /* summed device time, CUDA events on the launch stream */
   int64_t launches[RSV_KERNEL_KINDS];
   double bytes[RSV_KERNEL_KINDS];     /* summed algorithmic HBM bytes (each operand read or written once) */
+  /* The Krylov control step wherever it runs (fused into the second pass or
+   * launched), timed on the device (%globaltimer, first to last instruction of
+   * the step; the fused tail's arrival count is outside): all steps, and those
+   * that evaluated the small exponential (convergence test, partial step). */
+  double control_step_ms;
+  int64_t control_steps;
+  double control_check_ms;
+  int64_t control_checks;
 } rsv_kernel_times;
 
 /* ---- context -------------------------------------------------------------- */

@@ -40,7 +40,7 @@ class Problem_(C.Structure):
 class Config_(C.Structure):
     _fields_ = [("dt_ns", C.c_int32), ("precision", C.c_int32), ("krylov_tol", C.c_double),
                 ("m_max", C.c_int32), ("max_substeps", C.c_int32), ("obs_stride", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("flags", C.c_int32)]
 
 
 class Stats_(C.Structure):
@@ -50,7 +50,7 @@ class Stats_(C.Structure):
                 ("tile_order_bits", C.c_int32), ("krylov_dim_max", C.c_int32), ("strided_tile_bits", C.c_int32)]
 
 
-KERNEL_KINDS = ("pass_first", "pass_second", "control", "combine")
+KERNEL_KINDS = ("pass_first", "pass_second", "control", "combine", "setup")
 
 
 class ServerConfig_(C.Structure):
@@ -59,7 +59,9 @@ class ServerConfig_(C.Structure):
 
 
 class KernelTimes_(C.Structure):
-    _fields_ = [("ms", C.c_double * 4), ("launches", C.c_int64 * 4), ("bytes", C.c_double * 4)]
+    _fields_ = [("ms", C.c_double * 5), ("launches", C.c_int64 * 5), ("bytes", C.c_double * 5),
+                ("control_step_ms", C.c_double), ("control_steps", C.c_int64),
+                ("control_check_ms", C.c_double), ("control_checks", C.c_int64)]
 
 
 _lib = None
@@ -210,7 +212,11 @@ class ProblemArgs:
         return cls(p.positions, p.c6, p.t_ns, p.omega, p.delta, p.phi, initial_state)
 
 
-def make_config(dt_ns, precision="c128", krylov_tol=0.0, m_max=0, max_substeps=0, obs_stride=1) -> Config_:
+FLAG_CONTROL_LAUNCH = 1
+
+
+def make_config(dt_ns, precision="c128", krylov_tol=0.0, m_max=0, max_substeps=0, obs_stride=1,
+                control_launch=False) -> Config_:
     c = Config_()
     c.dt_ns = int(dt_ns)
     c.precision = precision_code(precision)
@@ -218,5 +224,5 @@ def make_config(dt_ns, precision="c128", krylov_tol=0.0, m_max=0, max_substeps=0
     c.m_max = int(m_max)
     c.max_substeps = int(max_substeps)
     c.obs_stride = int(obs_stride)
-    c.reserved = 0
+    c.flags = FLAG_CONTROL_LAUNCH if control_launch else 0
     return c

@@ -205,7 +205,7 @@ class Solver:
     """rsv_solver: one problem resident on the device, advanced step by step."""
 
     def __init__(self, ctx: Context, problem, dt_ns: int, precision="c128", krylov_tol=0.0, m_max=0,
-                 max_substeps=0, obs_stride=1, initial_state=None):
+                 max_substeps=0, obs_stride=1, initial_state=None, control_launch=False):
         self.ctx = ctx
         self.precision = precision_code(precision)
         init = None
@@ -213,7 +213,7 @@ class Solver:
             init = np.ascontiguousarray(np.asarray(initial_state, dtype=amp_dtype(precision)))
         self._pa = L.ProblemArgs.from_problem(problem, init)
         self.n = self._pa.n
-        self._cfg = L.make_config(dt_ns, precision, krylov_tol, m_max, max_substeps, obs_stride)
+        self._cfg = L.make_config(dt_ns, precision, krylov_tol, m_max, max_substeps, obs_stride, control_launch)
         self._h = C.c_void_p()
         check(L.lib().rsv_solver_create(ctx.handle, C.byref(self._pa.struct), C.byref(self._cfg),
                                         C.byref(self._h)))
@@ -271,11 +271,16 @@ class Solver:
         check(L.lib().rsv_solver_set_profiling(self._h, 1 if on else 0))
 
     def kernel_times(self) -> dict:
-        """{kind: {"ms", "launches", "bytes"}} accumulated while profiling was on."""
+        """{kind: {"ms", "launches", "bytes"}} accumulated while profiling was on,
+        and "control_step": the Krylov control step's device time wherever it
+        ran ({"ms", "steps", "check_ms", "checks"})."""
         t = L.KernelTimes_()
         check(L.lib().rsv_solver_kernel_times(self._h, C.byref(t)))
-        return {k: {"ms": t.ms[i], "launches": t.launches[i], "bytes": t.bytes[i]}
-                for i, k in enumerate(L.KERNEL_KINDS)}
+        out = {k: {"ms": t.ms[i], "launches": t.launches[i], "bytes": t.bytes[i]}
+               for i, k in enumerate(L.KERNEL_KINDS)}
+        out["control_step"] = {"ms": t.control_step_ms, "steps": t.control_steps, "check_ms": t.control_check_ms,
+                               "checks": t.control_checks}
+        return out
 
     def close(self):
         if self._h:

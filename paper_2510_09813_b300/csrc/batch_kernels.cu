@@ -48,6 +48,7 @@ namespace {
 
 constexpr int kBK = 8;   // vectors per thread of a full chunk (2^11 vectors / 256 threads)
 constexpr int kBKK = 3;  // register bits of a full chunk
+constexpr int kLoadBatch = 4;  // global loads issued together ahead of their stores
 
 // ---- thread-block cluster helpers (distributed shared memory) ----
 __device__ __forceinline__ unsigned cluster_rank() {
@@ -138,7 +139,7 @@ __device__ void chunk_row(Shared<Real>& s, int n, int T, int64_t c, int lane) {
 // whole vector (n <= TB), so the Lanczos sums are taken here.
 template <typename Real, bool PHI, bool COOP, typename Acc>
 __device__ void pass_a(Shared<Real>& s, Vec* s_x, const Real* s_q, int n, int T, int64_t c, const Vec* src,
-                       Vec* basis_j, const Vec* basis_prev, Vec* u, bool has_prev, Real a, Real sc, Real bprev,
+                       Vec* __restrict__ basis_j, const Vec* __restrict__ basis_prev, Vec* u, bool has_prev, Real a, Real sc, Real bprev,
                        bool reduce, Acc& r0, Acc& r1, Acc& r2) {
   constexpr int V = CplxT<Real>::kLogVec;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -232,29 +233,37 @@ __device__ void pass_b(Shared<Real>& s, Vec* s_x, int n, const Vec* basis_j, Vec
   const int cbv = VB - h;                  // contiguous vector bits of a segment
   const int lowmask = (1 << cbv) - 1;
   const int64_t nsc = int64_t(1) << h;
+  auto vidx_of = [&](int t, int64_t g) -> int64_t {
+    return ((int64_t)(t >> cbv) << VB) | (g << cbv) | (t & lowmask);
+  };
   for (int64_t g = g0; g < nsc; g += gstep) {
-    Vec x[kBK];
-    int64_t vidx[kBK];
+    {
+      Vec x[kBK];
 #pragma unroll
-    for (int k = 0; k < kBK; ++k) {
-      const int t = tid | (k << 8);
-      vidx[k] = ((int64_t)(t >> cbv) << VB) | (g << cbv) | (t & lowmask);
-      x[k] = ld_vec<COOP>(basis_j, vidx[k]);
-      sts_vec(s_x, t, x[k]);
+      for (int k = 0; k < kBK; ++k) x[k] = ld_vec<COOP>(basis_j, vidx_of(tid | (k << 8), g));
+#pragma unroll
+      for (int k = 0; k < kBK; ++k) sts_vec(s_x, tid | (k << 8), x[k]);
     }
     __syncthreads();
+    // the partial u of the segment, kLoadBatch loads ahead of their stores
 #pragma unroll
-    for (int k = 0; k < kBK; ++k) {
+    for (int k0 = 0; k0 < kBK; k0 += kLoadBatch) {
+      Vec y[kLoadBatch];
+#pragma unroll
+      for (int i = 0; i < kLoadBatch; ++i) y[i] = ld_vec<COOP>(u, vidx_of(tid | ((k0 + i) << 8), g));
+#pragma unroll
+      for (int i = 0; i < kLoadBatch; ++i) {
+      const int k = k0 + i;
       const int t = tid | (k << 8);
-      Vec y = ld_vec<COOP>(u, vidx[k]);
 #pragma unroll
       for (int r = 0; r < kBatchMaxAtoms - 11 + 1; ++r) {
         if (r >= h) break;
         const int tb = cbv + r;  // vector-index bit of amplitude bit TB + r
-        cmac<Real, PHI>(y, s.cp[TB + r][(t >> tb) & 1], lds_vec(s_x, t ^ (1 << tb)));
+        cmac<Real, PHI>(y[i], s.cp[TB + r][(t >> tb) & 1], lds_vec(s_x, t ^ (1 << tb)));
       }
-      stg_vec(u, vidx[k], y);
-      reduce_vec<Real>(x[k], y, r0, r1, r2);
+      stg_vec(u, vidx_of(t, g), y[i]);
+      reduce_vec<Real>(lds_vec(s_x, t), y[i], r0, r1, r2);
+      }
     }
     __syncthreads();
   }
@@ -286,7 +295,7 @@ __device__ void lanczos_iteration(Shared<Real>& s, Vec* s_x, const Real* s_q, in
 // |psi|^2 -> s.tot[0] and sum_b |psi_b|^2 b_q -> s.tot[1 + q]. Products are
 // exact (TwoProduct) and sums compensated.
 template <typename Real, bool COOP>
-__device__ void combine_observe(Shared<Real>& s, int n, int T, Vec* psi, const Vec* basis, int64_t vstride, int m,
+__device__ void combine_observe(Shared<Real>& s, int n, int T, Vec* psi, const Vec* __restrict__ basis, int64_t vstride, int m,
                                 bool combine, unsigned rank, unsigned ncl) {
   using Acc = typename AccFor<Real>::type;
   constexpr int V = CplxT<Real>::kLogVec;

@@ -21,6 +21,19 @@ constexpr int kStridedTileBitsF = 13;          // complex64: 2^13 amplitudes
 constexpr int kStridedTileBitsD = 12;          // complex128: 2^12 amplitudes
 constexpr int kStridedStages = 3;
 
+// Krylov control step of one Lanczos iteration (krylov_control.cuh).
+struct ChebWork;
+struct ScalarArgs {
+  KState* ks;
+  ChebWork* cache;    // device: the kept expansion, carried between launches
+  const double* partials;
+  int nparts;
+  int m_max;
+  int check_from;     // first Krylov dimension at which convergence is tested
+  double tol;         // relative tolerance p of the step
+  double breakdown;   // relative breakdown threshold for beta
+};
+
 struct TileArgs {
   int n;         // atoms = state bits
   int L;         // tile bits
@@ -44,6 +57,10 @@ struct TileArgs {
   double* partials;      // [grid][3]
   int* err;              // device error word: bit 0 = a bounded wait timed out
   const void* diag;      // first pass: [num_tiles][kDiagStride] diagonal half tables (working precision)
+  // Last pass of a Lanczos iteration with ctl.ks set: the CTA that finishes
+  // last runs the Krylov control step with these arguments (partials are this
+  // pass's), instead of a separate scalar launch.
+  ScalarArgs ctl;
 };
 
 // Per-tile diagonal half tables (diag_kernels.cu). For the contiguous tile
@@ -86,20 +103,9 @@ cudaError_t launch_strided(const TileArgs& args, const TileMaps* maps, bool lanc
 bool encode_tile_map(CUtensorMap* out, const void* base, const TileArgs& g, bool c64);
 
 // Krylov control kernels (krylov_kernels.cu).
-struct ChebWork;
 // Bytes of the device buffer a solver keeps for the control kernel's reused
 // Chebyshev expansion (zero-filled before first use).
 size_t cheb_cache_bytes();
-struct ScalarArgs {
-  KState* ks;
-  ChebWork* cache;    // device: the kept expansion, carried between launches
-  const double* partials;
-  int nparts;
-  int m_max;
-  int check_from;     // first Krylov dimension at which convergence is tested
-  double tol;         // relative tolerance p of the step
-  double breakdown;   // relative breakdown threshold for beta
-};
 cudaError_t launch_scalar(const ScalarArgs& a, cudaStream_t stream);
 
 struct BeginArgs {

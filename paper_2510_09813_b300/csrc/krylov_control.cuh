@@ -26,6 +26,12 @@ namespace rsv {
 // ---------------------------------------------------------------------------
 constexpr int kControlThreads = 128;
 
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
 struct ControlSmem {
   double part[3][kControlThreads / 32];
   double al[kMaxKrylov], be[kMaxKrylov + 1];
@@ -35,7 +41,7 @@ struct ControlSmem {
 
 // Threads 0 .. kControlThreads-1 of the calling CTA run it (the others must
 // not); they meet at named barrier 1. `w` is shared memory of the CTA.
-__device__ inline void krylov_control(const ScalarArgs& A, ControlSmem& w) {
+static __device__ __noinline__ void krylov_control(const ScalarArgs& A, ControlSmem& w) {
   double (&s_part)[3][kControlThreads / 32] = w.part;
   double* s_al = w.al;
   double* s_be = w.be;
@@ -44,13 +50,14 @@ __device__ inline void krylov_control(const ScalarArgs& A, ControlSmem& w) {
   ChebWork& s_w = w.cw;
   KState* ks = A.ks;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint64_t t_start = global_ns();
   // ---- loads, all issued before any of them is used ----
   const int status0 = ks->status;
   const int j = ks->j;
   double v[3] = {0.0, 0.0, 0.0};
   for (int p = tid; p < A.nparts; p += kControlThreads) {
 #pragma unroll
-    for (int i = 0; i < 3; ++i) v[i] += A.partials[(int64_t)p * 3 + i];
+    for (int i = 0; i < 3; ++i) v[i] += __ldcg(A.partials + (int64_t)p * 3 + i);  // other CTAs' stores
   }
   const int m = j + 1;
   const bool maybe_check = m >= A.check_from || m >= A.m_max;
@@ -174,6 +181,50 @@ __device__ inline void krylov_control(const ScalarArgs& A, ControlSmem& w) {
     ks->beta_prev = beta;
     ks->j = j + 1;
   }
+  if (lane == 0) {
+    const uint64_t dt = global_ns() - t_start;
+    ks->ctl_ns += dt;
+    ks->ctl_steps += 1;
+    if (check) {
+      ks->chk_ns += dt;
+      ks->chk_steps += 1;
+    }
+  }
+}
+
+// Tail of the last streaming pass of a Lanczos iteration, reached by every
+// thread of a CTA after its last block barrier (red: the warps' three partial
+// sums). Thread 0 stores the CTA's sums; with A.ks set (the control step
+// fused into the pass), it then counts the CTA in ks->arrivals, and the CTA
+// that arrives last runs krylov_control in `ring`, the pass's shared-memory
+// ring, whose copies have all landed. The usual last-block pattern: each CTA
+// fences its stores before its arrival, the last one fences after it. After a
+// timed-out wait (error word set) the step is skipped; the host reports it.
+template <int kWarps>
+__device__ __forceinline__ void pass_tail(const ScalarArgs& A, double* partials, const double (&red)[3][kWarps],
+                                          const int* err, unsigned char* ring) {
+  __shared__ int s_run;
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int v = 0; v < 3; ++v) {
+      double sum = 0.0;
+      for (int w = 0; w < kWarps; ++w) sum += red[v][w];
+      partials[(int64_t)blockIdx.x * 3 + v] = sum;
+    }
+    int run = 0;
+    if (A.ks) {
+      __threadfence();
+      if (atomicAdd(&A.ks->arrivals, 1u) == gridDim.x - 1) {
+        __threadfence();
+        A.ks->arrivals = 0;  // every CTA of this launch has counted itself
+        run = *reinterpret_cast<const volatile int*>(err) == 0;
+      }
+    }
+    s_run = run;
+  }
+  if (!A.ks) return;  // uniform over the launch
+  __syncthreads();
+  if (s_run && threadIdx.x < kControlThreads) krylov_control(A, *reinterpret_cast<ControlSmem*>(ring));
 }
 
 }  // namespace rsv

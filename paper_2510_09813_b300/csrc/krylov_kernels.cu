@@ -66,6 +66,7 @@ __global__ void __launch_bounds__(kThreads) begin_kernel(const BeginArgs A) {
       ks->form_s = b0 > 0.0 ? 1.0 / b0 : 0.0;
       ks->beta_prev = 0.0;
       ks->tnorm = 0.0;
+      ks->arrivals = 0;
       ks->j = 0;
       ks->m = 0;
       ks->status = b0 > 0.0 ? kContinue : kIdle;

@@ -349,24 +349,50 @@ __device__ inline KrylovDecision krylov_decide(const double* al, const double* b
     d.status = kDone;
     d.tau_take = tau_rem;
   } else if (m >= m_max) {
-    double t = tau_rem, t_bad = tau_rem;
-    for (int it = 0; it < 64; ++it) {
-      t_bad = t;
-      t *= 0.5;
+    // The largest t < tau_rem whose estimate meets tol. The estimate falls
+    // like a power of t (t^m for small t), so each guess is a secant step on
+    // log err against log t towards 0.85 tol, from the failing end of the
+    // bracket [t_lo meets tol, t_hi does not] with the bracket's slope; a
+    // guess outside the bracket is replaced by its geometric middle. The search
+    // stops once an accepted t has an estimate of at least 0.6 tol or the
+    // bracket is within 3%: two or three evaluations where halving and four
+    // bisections took six or seven. Guesses are FP32 (only t_lo's FP64
+    // evaluation decides).
+    double t_hi = tau_rem, e_hi = d.err, t_lo = 0.0, e_lo = 0.0;
+    float slope = (float)m;
+    bool ur_at_lo = false;
+    for (int it = 0; it < 24; ++it) {
+      double t = t_hi * (double)exp2f(log2f(0.85f * (float)(tol / e_hi)) / slope);
+      if (!(t > t_lo && t < t_hi)) t = t_lo > 0.0 ? sqrt(t_lo * t_hi) : 0.25 * t_hi;
       cheb_expm_e1(al, be, m, t, ur, ui, w);
-      if (beta * hypot(ur[m - 1], ui[m - 1]) <= tol) break;
+      const double e = beta * hypot(ur[m - 1], ui[m - 1]);
+      ur_at_lo = e <= tol;
+      if (ur_at_lo) {
+        t_lo = t;
+        e_lo = e;
+        if (e >= 0.6 * tol || t_hi <= 1.03 * t_lo) break;
+      } else {
+        t_hi = t;
+        e_hi = e;
+      }
+      if (t_lo > 0.0 && e_lo > 0.0 && e_hi > e_lo) slope = log2f((float)(e_hi / e_lo)) / log2f((float)(t_hi / t_lo));
+      if (!(slope >= 0.5f)) slope = 0.5f;
     }
-    for (int it = 0; it < 4; ++it) {
-      const double tm = sqrt(t * t_bad);
-      cheb_expm_e1(al, be, m, tm, ur, ui, w);
-      const double em = beta * hypot(ur[m - 1], ui[m - 1]);
-      if (em <= tol) t = tm;
-      else t_bad = tm;
+    if (!(t_lo > 0.0)) {
+      // not found in the budget (an estimate that does not fall with t):
+      // halve until it meets tol, as a last resort
+      t_lo = t_hi;
+      for (int it = 0; it < 64; ++it) {
+        t_lo *= 0.5;
+        cheb_expm_e1(al, be, m, t_lo, ur, ui, w);
+        if (beta * hypot(ur[m - 1], ui[m - 1]) <= tol) break;
+      }
+      ur_at_lo = true;
     }
-    cheb_expm_e1(al, be, m, t, ur, ui, w);
+    if (!ur_at_lo) cheb_expm_e1(al, be, m, t_lo, ur, ui, w);
     d.err = beta * hypot(ur[m - 1], ui[m - 1]);
     d.status = kDonePartial;
-    d.tau_take = t;
+    d.tau_take = t_lo;
   }
   return d;
 }

@@ -46,9 +46,12 @@ struct KState {
   int64_t total_iterations;
   int64_t total_substeps;
   int32_t error;                 // set by kernels whose bounded waits timed out
-  int32_t pad_i;
+  uint32_t arrivals;             // CTAs of the running last pass that have finished (fused control)
   double tnorm;                  // Gershgorin bound of T_m so far (max row sum), reset per Krylov space
-  double pad_[5];
+  // device time of the control step (%globaltimer ns), over the solver's life
+  uint64_t ctl_ns, ctl_steps;    // every step that did work
+  uint64_t chk_ns, chk_steps;    // steps that evaluated the small exponential
+  double pad_[1];
   // --- values consumed by the next "first" pass ---
   double form_a;                 // alpha_{j-1} (0 for j = 0)
   double form_s;                 // 1 / beta_j (1 / |psi| for j = 0)
@@ -61,7 +64,7 @@ struct KState {
 };
 constexpr int kStatusBytes = 128;
 static_assert(sizeof(int32_t) * 6 + sizeof(double) * 5 + sizeof(int64_t) * 2 + sizeof(double) * 1 +
-                  sizeof(double) * 5 == kStatusBytes,
+                  sizeof(uint64_t) * 4 + sizeof(double) * 1 == kStatusBytes,
               "status block layout");
 
 template <typename Real>

@@ -530,7 +530,8 @@ struct rsv_solver {
   std::vector<CUtensorMap> map_basis;  // strided-pass tensor maps over basis[j]
   CUtensorMap map_u[2];                // ... over the two work vectors
   KState* d_ks = nullptr;
-  ChebWork* d_cheb = nullptr;  // the control kernel's kept Chebyshev expansion
+  ChebWork* d_cheb = nullptr;  // the control step's kept Chebyshev expansion
+  bool fused_control = true;  // the control step runs in the last pass (not RSV_FLAG_CONTROL_LAUNCH)
   double* d_part = nullptr;
   double* d_cpart = nullptr;
   double* d_occ = nullptr;   // [max_rows][n]
@@ -566,6 +567,7 @@ struct rsv_solver {
     std::vector<char> zero_ks(sizeof(KState), 0);
     RSV_CUDA(cudaMemcpyAsync(d_ks, zero_ks.data(), sizeof(KState), cudaMemcpyHostToDevice, stream));
     RSV_CUDA(cudaMemsetAsync(d_cheb, 0, cheb_cache_bytes(), stream));
+    for (auto& v : ctl_seen) v = 0;
     done = 0;
     rows = 0;
     last_m = 0;
@@ -665,8 +667,23 @@ struct rsv_solver {
   rsv_status read_status() {
     RSV_CUDA(cudaMemcpyAsync(h_ks, d_ks, kStatusBytes, cudaMemcpyDeviceToHost, stream));
     RSV_CUDA(cudaStreamSynchronize(stream));
-    if (profiling) drain_timings();
+    if (profiling) {
+      drain_timings();
+      account_control();
+    }
     return RSV_OK;
+  }
+
+  // The device's control-step counters (KState, zeroed with the state) as
+  // last read, and what profiling has added up from them.
+  uint64_t ctl_seen[4] = {0, 0, 0, 0};
+  uint64_t ctl_acc[4] = {0, 0, 0, 0};
+  void account_control() {
+    const uint64_t cur[4] = {h_ks->ctl_ns, h_ks->ctl_steps, h_ks->chk_ns, h_ks->chk_steps};
+    for (int i = 0; i < 4; ++i) {
+      ctl_acc[i] += cur[i] >= ctl_seen[i] ? cur[i] - ctl_seen[i] : cur[i];  // zeroed by a rewind
+      ctl_seen[i] = cur[i];
+    }
   }
 
   double vec_bytes() const { return (double)dim * (double)amp_bytes(precision); }
@@ -695,7 +712,7 @@ struct rsv_solver {
     ba.new_tau = new_tau;
     ba.occ_out = occ_row;
     ba.reset_only = reset_only;
-    return launch(RSV_KERNEL_CONTROL, 0.0, [&] { return launch_begin(ba, stream); });
+    return launch(RSV_KERNEL_SETUP, 0.0, [&] { return launch_begin(ba, stream); });
   }
 
   rsv_status record_row() {
@@ -720,7 +737,9 @@ struct rsv_solver {
   // Algorithmic bytes: first pass reads u_{j-1} (and v_{j-1} for j > 0) and
   // writes v_j and its output; the second pass reads v_j and the first pass's
   // output and writes u_j.
-  rsv_status iteration(int j, int step) {
+  // ctl: the control step to fuse into the iteration's last pass (nullptr: a
+  // separate scalar launch follows).
+  rsv_status iteration(int j, int step, const ScalarArgs* ctl) {
     void* u_in = j == 0 ? d_psi : d_u[(j - 1) & 1];
     void* u_out = d_u[j & 1];
     TileArgs a = base_args(plan.a, step);
@@ -730,6 +749,7 @@ struct rsv_solver {
     a.out = u_out;
     const double first_bytes = vec_bytes() * (j > 0 ? 4 : 3);
     if (!plan.two_pass) {
+      if (ctl) a.ctl = *ctl;
       RSV_TRY(launch(RSV_KERNEL_PASS_FIRST, first_bytes,
                      [&] { return launch_tile(a, nullptr, TileMode::kLanczosSingle, c64, phi, plan.grid_a, stream); }));
     } else {
@@ -738,6 +758,7 @@ struct rsv_solver {
       TileArgs b = base_args(plan.b, step);
       b.xin = basis[j];
       b.out = u_out;
+      if (ctl) b.ctl = *ctl;
       RSV_TRY(launch(RSV_KERNEL_PASS_SECOND, vec_bytes() * 3,
                      [&] {
                        TileMaps maps{map_basis[j], map_u[j & 1]};
@@ -752,7 +773,7 @@ struct rsv_solver {
   // partials of d_psi (left by the previous combine or observation).
   rsv_status evolve(int k, double tau) {
     RSV_TRY(begin(tau, 0, nullptr));
-    RSV_TRY(launch(RSV_KERNEL_CONTROL, 0.0, [&] {
+    RSV_TRY(launch(RSV_KERNEL_SETUP, 0.0, [&] {
       return launch_diag_table(d_sp + k, d_vmat, n, plan.a.L, plan.a.num_tiles, d_diag, c64, stream);
     }));
     const int m_max = cfg.m_max;
@@ -771,8 +792,12 @@ struct rsv_solver {
       int j = 0;
       bool finished = false;
       for (; j < m_max; ++j) {
-        RSV_TRY(iteration(j, k));
-        RSV_TRY(launch(RSV_KERNEL_CONTROL, 0.0, [&] { return launch_scalar(sa, stream); }));
+        if (fused_control) {
+          RSV_TRY(iteration(j, k, &sa));
+        } else {
+          RSV_TRY(iteration(j, k, nullptr));
+          RSV_TRY(launch(RSV_KERNEL_CONTROL, 0.0, [&] { return launch_scalar(sa, stream); }));
+        }
         if (j + 1 >= check_from) {
           RSV_TRY(read_status());
           if (h_ks->error) return fail(RSV_ERR_TIMEOUT, "a device-side wait timed out (kernel aborted)");
@@ -1372,6 +1397,7 @@ static rsv_status solver_create(rsv_ctx* ctx, const rsv_problem* problem, const 
   if (cfg.krylov_tol <= 0.0) cfg.krylov_tol = cfg.precision == RSV_C64 ? 1e-7 : 1e-12;
   if (cfg.max_substeps <= 0) cfg.max_substeps = 64;
   if (cfg.obs_stride < 0) return fail(RSV_ERR_INVALID_ARG, "obs_stride must be >= 0");
+  if (cfg.flags & ~RSV_FLAG_CONTROL_LAUNCH) return fail(RSV_ERR_INVALID_ARG, "unknown flags");
   const int n = problem->n_atoms;
   if (cfg.precision == RSV_C128 && n > 30) return fail(RSV_ERR_INVALID_ARG, "n_atoms too large for complex128");
   std::lock_guard<std::mutex> lk(ctx->mu);
@@ -1389,6 +1415,7 @@ static rsv_status solver_create(rsv_ctx* ctx, const rsv_problem* problem, const 
   s->c64 = cfg.precision == RSV_C64;
   s->dim = int64_t(1) << n;
   s->cfg = cfg;
+  s->fused_control = !(cfg.flags & RSV_FLAG_CONTROL_LAUNCH);
   s->plan = make_plan(n, s->c64, ctx->num_sms);  // strided-pass shape tuned below
   RSV_TRY(step_params(problem, cfg.dt_ns, s->h_sp));
   s->nsteps = (int)s->h_sp.size();
@@ -1580,13 +1607,21 @@ rsv_status rsv_solver_set_profiling(rsv_solver* s, int32_t on) {
   RSV_CUDA(cudaStreamSynchronize(s->stream));
   s->drain_timings();
   s->profiling = on != 0;
-  if (s->profiling) s->ktimes = rsv_kernel_times{};
+  if (s->profiling) {
+    s->ktimes = rsv_kernel_times{};
+    RSV_TRY(s->read_status());  // the control counters' starting point
+    for (auto& v : s->ctl_acc) v = 0;
+  }
   return RSV_OK;
 }
 
 rsv_status rsv_solver_kernel_times(const rsv_solver* s, rsv_kernel_times* out) {
   if (!s || !out) return fail(RSV_ERR_INVALID_ARG, "NULL argument");
   *out = s->ktimes;
+  out->control_step_ms = s->ctl_acc[0] * 1e-6;
+  out->control_steps = (int64_t)s->ctl_acc[1];
+  out->control_check_ms = s->ctl_acc[2] * 1e-6;
+  out->control_checks = (int64_t)s->ctl_acc[3];
   return RSV_OK;
 }
 

@@ -38,11 +38,14 @@
 #include <type_traits>
 
 #include "kernels.h"
+#include "krylov_control.cuh"
 #include "rsv_common.cuh"
 #include "tma.cuh"
 #include "vec_ops.cuh"
 
 namespace rsv {
+
+static_assert(sizeof(ControlSmem) <= (size_t)kStridedStages * 65536, "the control step fits the idle ring");
 
 template <typename Real>
 struct StridedCfg {
@@ -258,11 +261,7 @@ __global__ void __launch_bounds__(kTileThreads, 1)
       mbar_wait(&full[ip % kStridedStages], (ip / kStridedStages) & 1);
   }
   __syncthreads();
-  if (LANCZOS && tid < 3) {
-    double sum = 0.0;
-    for (int w = 0; w < kConsumerWarps; ++w) sum += s_red[tid][w];
-    args.partials[(int64_t)blockIdx.x * 3 + tid] = sum;
-  }
+  if (LANCZOS) pass_tail(args.ctl, args.partials, s_red, args.err, smem);
 }
 
 template <typename Real, bool LANCZOS, bool PHI>

@@ -31,11 +31,14 @@
 #include <type_traits>
 
 #include "kernels.h"
+#include "krylov_control.cuh"
 #include "rsv_common.cuh"
 #include "tma.cuh"
 #include "vec_ops.cuh"
 
 namespace rsv {
+
+static_assert(sizeof(ControlSmem) <= (size_t)kStages * 2 * 32768, "the control step fits the idle ring");
 
 template <typename Real>
 struct TileCfg {
@@ -367,11 +370,7 @@ __global__ void __launch_bounds__(kTileThreads, 1)
   }
   // every thread of the CTA reaches this point: all waits above are bounded
   __syncthreads();
-  if (LANCZOS && LAST && tid < 3) {
-    double sum = 0.0;
-    for (int w = 0; w < kConsumerWarps; ++w) sum += s_red[tid][w];
-    args.partials[(int64_t)blockIdx.x * 3 + tid] = sum;
-  }
+  if (LANCZOS && LAST) pass_tail(args.ctl, args.partials, s_red, args.err, smem);
 }
 
 // ---------------------------------------------------------------------------

@@ -358,6 +358,45 @@ def test_krylov_restarts_match(ctx):
     assert O.norm_difference(psi, ref) <= 1e-9
 
 
+@pytest.mark.parametrize("n,prec,shape", [(10, "c64", None), (19, "c128", None), (22, "c64", (5, 0, 1)),
+                                           (22, "c128", (4, 2, 0)), (22, "c128", (3, 2, 1))])
+def test_fused_control_matches_control_launch(monkeypatch, n, prec, shape):
+    """The Krylov control step run by the last CTA of each iteration's last
+    pass (the default) against the same step as a launch of its own
+    (RSV_FLAG_CONTROL_LAUNCH): identical arithmetic, so identical states and
+    Krylov statistics, bit for bit, on the single-pass kernel and both
+    second-pass kernels; no control launches when fused. Then the state
+    against the oracle."""
+    A = api()
+    if shape:
+        force_shape(monkeypatch, *shape)
+    c = A.Context(0)
+    prob = W.random_box(seed=11, n=n, side_um=5.0 * math.ceil(math.sqrt(n)), t_ns=40)
+    out = {}
+    for launch in (False, True):
+        s = A.Solver(c, prob, 10, prec, control_launch=launch)
+        s.set_profiling(True)
+        s.run_to_end()
+        kt = s.kernel_times()
+        out[launch] = (s.state(), s.stats(), kt["control"]["launches"], kt["pass_first"]["launches"])
+        s.close()
+    (psi_f, st_f, ctl_f, nf), (psi_l, st_l, ctl_l, nl) = out[False], out[True]
+    assert np.array_equal(psi_f.view(np.uint8), psi_l.view(np.uint8))
+    for k in ("krylov_iterations", "substeps", "max_error_estimate"):
+        assert st_f[k] == st_l[k], k
+    assert ctl_f == 0 and ctl_l == nl == nf >= st_f["krylov_iterations"] > 0  # setup launches are apart
+    if shape:
+        assert st_f["segment_bits"] == shape[0] and st_f["tile_order_bits"] == shape[1]
+    ref, _ = oracle_evolve(prob, 10)
+    assert O.infidelity(psi_f.astype(np.complex128), ref) <= INFID_TOL[prec]
+    bad = A.L.make_config(10, prec)
+    bad.flags = 2
+    pa = A.L.ProblemArgs.from_problem(prob, None)
+    h = A.C.c_void_p()
+    assert A.L.lib().rsv_solver_create(c.handle, A.C.byref(pa.struct), A.C.byref(bad), A.C.byref(h)) == -1
+    c.close()
+
+
 def test_zero_drive_diagonal(ctx):
     """Omega = 0 from a superposition: H is diagonal but the Krylov space still grows."""
     n, t_ns = 10, 50
