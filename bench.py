@@ -43,6 +43,7 @@ sys.path.insert(0, ROOT)
 N_ATOMS = 28
 BATCH_M_MAX = -1  # Krylov depth autotuned on a sample of the registers
 SERVE_ARENA = 160 << 30
+SERVE_BATCH_ATOMS = 16  # the batched lane's size limit (complex64 requests only)
 SERVE_REQUESTS = 200
 SERVE_FIFO_REQUESTS = 64  # the one-at-a-time complex128 baseline replays the first 64
 SERVE_MAX_ATOMS = 20
@@ -318,8 +319,8 @@ def serving_leg(api, W, device: int, count: int, n_hi: int):
     reqs = W.serving_stream(seed=5, count=count, n_hi=n_hi)
     ctx = api.Context(device, arena_bytes=SERVE_ARENA)
 
-    def replay(slots, force_c128, time_scale=1.0, count=None):
-        srv = api.Server(ctx, slots=slots, max_bypass_s=-1 if slots == 1 else 0.0)
+    def replay(slots, force_c128, time_scale=1.0, count=None, batch_atoms=0):
+        srv = api.Server(ctx, slots=slots, max_bypass_s=-1 if slots == 1 else 0.0, batch_atoms=batch_atoms)
         t0 = time.perf_counter()
         tickets = []
         for r in reqs[:count]:
@@ -349,11 +350,21 @@ def serving_leg(api, W, device: int, count: int, n_hi: int):
     rate = 0.7 * mixed["solves_per_s"]
     sustainable = replay(4, False, time_scale=200.0 / rate)
     sustainable["offered_per_s"] = rate
+    # with the batched lane: queued complex64 requests of at most 16 atoms
+    # share one persistent launch; a lone one, and complex128, stream
+    lane = {}
+    ba = min(n_hi, SERVE_BATCH_ATOMS)
+    lane = replay(4, False, batch_atoms=ba)
+    lane_rate = 0.7 * lane["solves_per_s"]
+    lane_70 = replay(4, False, time_scale=200.0 / lane_rate, batch_atoms=ba)
+    lane_70["offered_per_s"] = lane_rate
+    lane = {"continuous_batching_batched_lane": {"slots": 4, "batch_atoms": ba, **lane},
+            "continuous_batching_batched_lane_at_70pct_load": {"slots": 4, "batch_atoms": ba, **lane_70}}
     ctx.close()
     wl = SERVE_WORKLOAD if n_hi == 26 else SERVE_WORKLOAD.replace("U{12..26}", f"U{{12..{n_hi}}}")
     return {"workload": wl, "requests": count, "continuous_batching": {"slots": 4, **mixed},
             "one_at_a_time_c128": {"slots": 1, **fifo},
-            "continuous_batching_at_70pct_load": {"slots": 4, **sustainable}}
+            "continuous_batching_at_70pct_load": {"slots": 4, **sustainable}, **lane}
 
 
 CFG1_WORKLOAD = ("8-atom chain at 6 um, C6 = 5420158.53 rad um^6/us, Omega = 2 pi rad/us, delta = phi = 0, "
@@ -633,7 +644,10 @@ def ours(args):
             torch.distributed.barrier()
 
     solver.step(w0)
-    start_state = solver.state()  # host copy for the end-to-end leg (untimed)
+    # host copy for the end-to-end leg (untimed), in pinned memory as the
+    # end-to-end contract has it
+    start_state = torch.empty(2 ** N_ATOMS, dtype=torch.complex64, pin_memory=True).numpy()
+    start_state[:] = solver.state()
     it0 = solver.stats()["krylov_iterations"]
     l0 = solver.stats()["kernel_launches"]
     kt = {k: {"ms": 0.0, "launches": 0, "bytes": 0.0} for k in ("pass_first", "pass_second", "control", "combine", "setup")}

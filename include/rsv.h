@@ -490,9 +490,12 @@ RSV_API rsv_status rsv_lindblad_run(rsv_ctx* ctx, const rsv_problem* problem, co
 
 typedef struct {
   int32_t slots;        /* solves in flight at once, each on its own CUDA stream; default 4 */
-  int32_t batch_atoms;  /* 0: off. Else a request of at most this many atoms (<= 20) is solved together
-                           with the queued requests of the same size and config that fit (up to 64) by
-                           one batched launch (rsv_batch_*); pays off for bursts of like requests */
+  int32_t batch_atoms;  /* 0: off. Else a complex64 request of at most this many atoms (<= 20) is solved
+                           together with the queued complex64 requests of at most that many atoms and
+                           the same config (dt, tolerances, m_max, obs_stride; any size and duration)
+                           that fit, up to 64, by one batched launch (rsv_batch_*). A request with no
+                           such companion in the queue, and every complex128 request, runs on the
+                           streaming solver */
   size_t memory_bytes;  /* device bytes admitted solves may hold together. 0: the context arena's
                            free bytes at creation (capped context), else 90% of the device's free
                            memory */

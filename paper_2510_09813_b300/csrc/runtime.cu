@@ -19,6 +19,7 @@
 #include <map>
 #include <future>
 #include <thread>
+#include <tuple>
 #include <deque>
 #include <condition_variable>
 #include <memory>
@@ -425,10 +426,30 @@ int shape_override(int n, bool c64, int num_sms) {
 }
 
 // Tuned shape (pack_shape) of this register size and precision.
+// Tuned shapes are a property of the device and the register size, not of a
+// context: every context of the process on the same device shares them, so a
+// new context does not time the candidates again.
+std::mutex g_tuned_mu;
+std::map<std::tuple<int, int, int>, int> g_tuned;  // (device, n_atoms, complex64) -> shape
+
+bool tuned_lookup(rsv_ctx* ctx, int n, bool c64, int* shape) {
+  const auto key = std::make_pair(n, c64 ? 1 : 0);
+  auto it = ctx->tuned_segment.find(key);
+  if (it != ctx->tuned_segment.end()) {
+    *shape = it->second;
+    return true;
+  }
+  std::lock_guard<std::mutex> lk(g_tuned_mu);
+  auto g = g_tuned.find(std::make_tuple(ctx->device, n, c64 ? 1 : 0));
+  if (g == g_tuned.end()) return false;
+  ctx->tuned_segment[key] = *shape = g->second;
+  return true;
+}
+
 int shape_for(rsv_ctx* ctx, int n, bool c64) {
   if (const int o = shape_override(n, c64, ctx->num_sms)) return o;
-  auto it = ctx->tuned_segment.find({n, c64 ? 1 : 0});
-  return it == ctx->tuned_segment.end() ? pack_shape(kMinSegmentBits, 0, false) : it->second;
+  int shape = 0;
+  return tuned_lookup(ctx, n, c64, &shape) ? shape : pack_shape(kMinSegmentBits, 0, false);
 }
 
 // Candidates the tuner times: staged-z tiles with c in {4, 5} x f1_fast in
@@ -452,8 +473,8 @@ int tune_shape(rsv_ctx* ctx, cudaStream_t stream, int n, bool c64, StepParams* s
                void* z) {
   if (const int o = shape_override(n, c64, ctx->num_sms)) return o;
   const auto key = std::make_pair(n, c64 ? 1 : 0);
-  auto it = ctx->tuned_segment.find(key);
-  if (it != ctx->tuned_segment.end()) return it->second;
+  int known = 0;
+  if (tuned_lookup(ctx, n, c64, &known)) return known;
   int best = pack_shape(kMinSegmentBits, 0, false);
   float best_ms = 1e30f;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -490,6 +511,8 @@ int tune_shape(rsv_ctx* ctx, cudaStream_t stream, int n, bool c64, StepParams* s
   cudaEventDestroy(e1);
   cudaMemsetAsync(err_ptr(ks), 0, sizeof(int), stream);
   ctx->tuned_segment[key] = best;
+  std::lock_guard<std::mutex> lk(g_tuned_mu);
+  g_tuned[std::make_tuple(ctx->device, n, c64 ? 1 : 0)] = best;
   return best;
 }
 
@@ -553,9 +576,13 @@ struct rsv_solver {
   std::vector<char> init_host;  // caller's initial state (empty: |0...0>)
 
   // State <- initial state, step counter and recorded rows <- 0, row 0 recorded.
-  rsv_status reset_to_initial() {
+  // `direct`: the caller's initial state, copied straight to the device (a
+  // one-shot solver, which never rewinds and so keeps no host copy).
+  rsv_status reset_to_initial(const void* direct = nullptr) {
     const size_t vbytes = (size_t)dim * amp_bytes(precision);
-    if (!init_host.empty()) {
+    if (direct) {
+      RSV_CUDA(cudaMemcpyAsync(d_psi, direct, vbytes, cudaMemcpyHostToDevice, stream));
+    } else if (!init_host.empty()) {
       RSV_CUDA(cudaMemcpyAsync(d_psi, init_host.data(), vbytes, cudaMemcpyHostToDevice, stream));
     } else {
       RSV_CUDA(cudaMemsetAsync(d_psi, 0, vbytes, stream));
@@ -1383,8 +1410,10 @@ rsv_status rsv_sample(rsv_ctx* ctx, int32_t n_atoms, int32_t precision, const vo
   return RSV_OK;
 }
 
+// one_shot: the solver will be stepped to the end and never rewound (rsv_run,
+// served requests), so it keeps no host copy of the caller's initial state.
 static rsv_status solver_create(rsv_ctx* ctx, const rsv_problem* problem, const rsv_config* config,
-                                cudaStream_t stream, rsv_solver** out) {
+                                cudaStream_t stream, rsv_solver** out, bool one_shot = false) {
   g_last_error.clear();
   if (!ctx || !config || !out) return fail(RSV_ERR_INVALID_ARG, "NULL argument");
   *out = nullptr;
@@ -1490,11 +1519,11 @@ static rsv_status solver_create(rsv_ctx* ctx, const rsv_problem* problem, const 
       return fin(fail(RSV_ERR_CUDA, "upload failed"));
     cudaStreamSynchronize(s->stream);
   }
-  if (problem->initial_state) {
+  if (problem->initial_state && !one_shot) {
     const char* p = static_cast<const char*>(problem->initial_state);
     s->init_host.assign(p, p + vbytes);
   }
-  rsv_status r = s->reset_to_initial();
+  rsv_status r = s->reset_to_initial(one_shot ? problem->initial_state : nullptr);
   if (r != RSV_OK) return fin(r);
   ctx->solvers.insert(s);
   *out = s;
@@ -1668,7 +1697,7 @@ rsv_status rsv_run(rsv_ctx* ctx, const rsv_problem* problem, const rsv_config* c
   if (!out) return fail(RSV_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
   rsv_solver* s = nullptr;
-  RSV_TRY(rsv_solver_create(ctx, problem, config, &s));
+  RSV_TRY(solver_create(ctx, problem, config, nullptr, &s, /*one_shot=*/true));
   rsv_status st = rsv_solver_step(s, s->nsteps);
   if (st != RSV_OK) {
     rsv_solver_destroy(s);
@@ -2999,12 +3028,20 @@ struct rsv_server {
     return queue.end();
   }
 
-  // Requests of up to batch_atoms atoms with the same size and config are taken
-  // from the queue together and solved by one batched-kernel launch (every step
-  // on the device, no host round trip per iteration).
-  bool batchable(const ServeRequest* r) const { return r->prob.n_atoms <= batch_atoms; }
+  // Requests of up to batch_atoms atoms with the same config are taken from the
+  // queue together and solved by one batched-kernel launch (every step on the
+  // device, no host round trip per iteration); sizes and durations may differ,
+  // since each register of a batch runs its own sequence. A request with no
+  // such companion queued runs on the streaming solver, which is faster for a
+  // single register than a batch of one.
+  // complex64 only: a complex128 batch runs FP64 arithmetic on one CTA (or one
+  // 4-CTA cluster) per register, which on this part is far slower than the
+  // streaming solver spread over every SM.
+  bool batchable(const ServeRequest* r) const {
+    return r->prob.n_atoms <= batch_atoms && r->cfg.precision == RSV_C64;
+  }
   static bool same_class(const ServeRequest* a, const ServeRequest* b) {
-    return a->prob.n_atoms == b->prob.n_atoms && std::memcmp(&a->cfg, &b->cfg, sizeof(rsv_config)) == 0;
+    return std::memcmp(&a->cfg, &b->cfg, sizeof(rsv_config)) == 0;
   }
 
   // Solves a group of like requests in one batched launch. On success the
@@ -3055,7 +3092,7 @@ struct rsv_server {
     cudaStream_t st = nullptr;
     RSV_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
     rsv_solver* s = nullptr;
-    const rsv_status c = solver_create(ctx, &r->prob, &r->cfg, st, &s);
+    const rsv_status c = solver_create(ctx, &r->prob, &r->cfg, st, &s, /*one_shot=*/true);
     if (c != RSV_OK) {
       cudaStreamDestroy(st);
       return c;
@@ -3091,7 +3128,7 @@ struct rsv_server {
         if (batchable(g[0])) {
           for (auto jt = queue.begin(); jt != queue.end() && (int)g.size() < kServeBatchMax;) {
             ServeRequest* q = *jt;
-            if (same_class(q, g[0]) && q->bytes <= budget - in_use) {
+            if (batchable(q) && same_class(q, g[0]) && q->bytes <= budget - in_use) {
               in_use += q->bytes;
               g.push_back(q);
               jt = queue.erase(jt);
@@ -3109,7 +3146,8 @@ struct rsv_server {
       }
       std::vector<rsv_result*> res(g.size(), nullptr);
       size_t group_charge = 0;  // equals the sum of the group's footprints
-      const rsv_status st = batchable(g[0]) ? serve_group(g, res, &group_charge) : serve(g[0], &res[0]);
+      const bool grouped = g.size() > 1;
+      const rsv_status st = grouped ? serve_group(g, res, &group_charge) : serve(g[0], &res[0]);
       const std::string err = st == RSV_OK ? std::string() : g_last_error;
       {
         std::lock_guard<std::mutex> lk(mu);
@@ -3128,7 +3166,7 @@ struct rsv_server {
           // bytes a result keeps stay charged until it is freed: the state of
           // a streaming result; a batched group's whole footprint, which the
           // shared batch's deleter releases with the group's last result
-          const bool group_held = batchable(g[0]) && st == RSV_OK;
+          const bool group_held = grouped && st == RSV_OK;
           const size_t kept = group_held ? q->bytes : (res[i] ? res[i]->charged : 0);
           in_use -= q->bytes - kept;
           --running;

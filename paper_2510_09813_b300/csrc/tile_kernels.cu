@@ -69,7 +69,7 @@ __global__ void __launch_bounds__(kTileThreads, 1)
 
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ __align__(8) uint64_t full[kStages], empty[kStages], formed[kStages];
-  __shared__ Real s_t[kStages][kDiagStride];  // the staged tile's diagonal half tables (first pass)
+  __shared__ __align__(128) Real s_t[kStages][kDiagStride];  // the staged tile's diagonal half tables (first pass)
   __shared__ Coef s_cp[kMaxAtoms][2];         // [amplitude bit][bit of the target], apply form
   __shared__ double s_red[3][kConsumerWarps];
 
@@ -142,18 +142,15 @@ __global__ void __launch_bounds__(kTileThreads, 1)
         return;
       }
     }
-    if (FIRST) {
-      // this tile's diagonal half tables (c == L: tile bits are amplitude bits [0, L))
-      const Real* row = static_cast<const Real*>(args.diag) + tile * kDiagStride;
-#pragma unroll
-      for (int i = lane; i < kDiagStride; i += 32) s_t[s][i] = row[i];
-      __syncwarp();
-    }
     if (lane == 0) {
       if (FIRST) {
-        // contiguous tile: amplitude offset tile << L
+        // contiguous tile: amplitude offset tile << L; its diagonal half tables
+        // (c == L: tile bits are amplitude bits [0, L)) ride on the same
+        // barrier, so no thread waits on a global load for them
         const size_t off = (size_t)tile * tile_bytes;
-        mbar_arrive_expect_tx(&full[s], tile_bytes * (has_prev ? 2 : 1));
+        constexpr uint32_t row_bytes = kDiagStride * sizeof(Real);
+        mbar_arrive_expect_tx(&full[s], tile_bytes * (has_prev ? 2 : 1) + row_bytes);
+        tma_load_1d(s_t[s], static_cast<const Real*>(args.diag) + tile * kDiagStride, row_bytes, &full[s]);
         tma_load_1d(stage_tile(s, 0), static_cast<const unsigned char*>(args.xin) + off, tile_bytes, &full[s]);
         if (has_prev)
           tma_load_1d(stage_tile(s, 1), static_cast<const unsigned char*>(args.xprev) + off, tile_bytes, &full[s]);

@@ -84,12 +84,19 @@ def test_results_alone_equal_in_mix(ctx):
         one.close()
 
 
-def test_batched_lane_groups_like_requests(ctx):
-    """With batch_atoms set, like requests queued together are solved by one
-    batched launch (they share admission and completion times) and give the
-    same results as each request served alone."""
-    probs = [W.random_knot_problem(np.random.Generator(np.random.PCG64([31, k])), 10, 100) for k in range(8)]
-    srv = api().Server(ctx, slots=1, batch_atoms=14)
+@pytest.mark.parametrize("sizes,t_ns", [([10] * 8, [100] * 8),
+                                         ([10, 13, 16, 11, 18, 12, 15, 14], [100, 60, 140, 80, 100, 120, 60, 90])])
+def test_batched_lane_groups_requests(ctx, sizes, t_ns):
+    """With batch_atoms set, requests of at most that many atoms and the same
+    config queued together are solved by one batched launch (they share
+    admission and completion times), whatever their sizes and durations. Each
+    result is bit for bit the request's own batched solve (a batch of one: a
+    register's computation does not depend on its batch neighbours), and
+    within the tolerance of the streaming solver; a request served alone
+    with nothing to group with runs on the streaming solver."""
+    probs = [W.random_knot_problem(np.random.Generator(np.random.PCG64([31, k])), n, t)
+             for k, (n, t) in enumerate(zip(sizes, t_ns))]
+    srv = api().Server(ctx, slots=1, batch_atoms=20)
     tickets = [srv.submit(p, 10, "c64", obs_stride=1) for p in probs]
     results = [srv.poll(t) for t in tickets]
     srv.close()
@@ -97,14 +104,24 @@ def test_batched_lane_groups_like_requests(ctx):
     # the first request may have started alone before the others were queued
     assert max(service.count(v) for v in service) >= 2
     for p, r in zip(probs, results):
-        one = api().Server(ctx, slots=1, batch_atoms=14)
-        alone = one.poll(one.submit(p, 10, "c64", obs_stride=1))
-        assert np.array_equal(alone.state(), r.state())
         ref = api().run(ctx, p, 10, "c64", obs_stride=1)
         assert O.infidelity(r.state().astype(np.complex128), ref.state().astype(np.complex128)) <= INFID_TOL["c64"]
-        for x in (alone, ref, r):
+        assert np.max(np.abs(r.occupations() - ref.occupations())) <= OCC_TOL["c64"]
+        if service.count(r.times()[1]) >= 2:
+            (own,) = api().run_batch(ctx, [p], 10, "c64", obs_stride=1)
+            assert np.array_equal(own.state(), r.state())
+            own.close()
+        else:
+            assert np.array_equal(ref.state(), r.state())
+        for x in (ref, r):
             x.close()
-        one.close()
+    one = api().Server(ctx, slots=1, batch_atoms=20)
+    alone = one.poll(one.submit(probs[0], 10, "c64", obs_stride=1))
+    ref = api().run(ctx, probs[0], 10, "c64", obs_stride=1)
+    assert np.array_equal(alone.state(), ref.state())
+    for x in (alone, ref):
+        x.close()
+    one.close()
 
 
 def test_served_result_matches_oracle(ctx):
