@@ -464,12 +464,14 @@ def config_legs(api, W, device: int, cfg1_oracle):
 
 
 PHI_WORKLOAD = ("the 28-atom random box with a laser phase: phi_i ~ U(-pi, pi) per atom, constant in time "
-                "(complex flip coefficients), c64, dt = 5 ns, m_max = 20; steady-state steps")
+                "(run in the gauge frame: real-coefficient passes between two phase passes), c64, dt = 5 ns, "
+                "m_max = 20; steady-state steps")
 
 
 def phi_leg(api, W, device: int, warm: int = TRANSIENT_STEPS, steps: int = 3):
-    """Steady-state Lanczos steps of the random box with phi != 0 (the flip
-    kernels' complex-coefficient variant), beside the phi = 0 headline."""
+    """Steady-state Lanczos steps of the random box with phi != 0 (the gauge
+    frame: psi <- U^dagger psi, the phi = 0 passes, psi <- U psi), beside the
+    phi = 0 headline."""
     import torch
     base = W.random_box(seed=3, n=N_ATOMS, t_ns=(warm + steps) * DT_NS)
     rng = np.random.Generator(np.random.PCG64(33))
@@ -495,7 +497,8 @@ def phi_leg(api, W, device: int, warm: int = TRANSIENT_STEPS, steps: int = 3):
     per = {k: round(kt[k]["ms"] / max(1, kt[k]["launches"]), 4) for k in ("pass_first", "pass_second", "combine")}
     return {"workload": PHI_WORKLOAD, "steps_per_s": steps / (ms / 1e3), "ms_per_step": ms / steps,
             "krylov_iterations_per_step": (st["krylov_iterations"] - it0) / steps,
-            "ms_per_launch": per, "krylov_error_estimate": st["max_error_estimate"]}
+            "ms_per_launch": per, "krylov_error_estimate": st["max_error_estimate"],
+            "phase_gauge_steps": st["phase_gauge_steps"], "setup_ms_per_step": round(kt["setup"]["ms"] / steps, 3)}
 
 
 def control_leg(api, ctx, prob, start_state, fused_kt, fused_step_ms, steps: int = 3):

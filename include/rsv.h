@@ -117,6 +117,8 @@ typedef struct {
   int32_t krylov_dim_max;     /* Krylov dimension cap in use (m_max; autotuned for batches created with m_max < 0) */
   int32_t strided_tile_bits;  /* strided pass: log2 amplitudes of its shared-memory tile (x-only tiles: 13 for
                                  complex64, 12 for complex128; tiles staging x and z: 12 / 11); 0 = one pass */
+  int64_t phase_gauge_steps;  /* time steps with a laser phase run in the gauge frame: psi <- U^dagger psi,
+                                 real-coefficient passes, psi <- U psi, U = exp(-i sum_i phi_i n_i) */
 } rsv_stats;
 
 /* Kernel classes of the time step, for rsv_solver_kernel_times. */

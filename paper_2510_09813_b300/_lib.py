@@ -47,7 +47,8 @@ class Stats_(C.Structure):
     _fields_ = [("steps", C.c_int64), ("krylov_iterations", C.c_int64), ("substeps", C.c_int64),
                 ("max_error_estimate", C.c_double), ("seconds", C.c_double), ("kernel_launches", C.c_int64),
                 ("tile_passes", C.c_int32), ("segment_bits", C.c_int32), ("l2_partner_bits", C.c_int32),
-                ("tile_order_bits", C.c_int32), ("krylov_dim_max", C.c_int32), ("strided_tile_bits", C.c_int32)]
+                ("tile_order_bits", C.c_int32), ("krylov_dim_max", C.c_int32), ("strided_tile_bits", C.c_int32),
+                ("phase_gauge_steps", C.c_int64)]
 
 
 KERNEL_KINDS = ("pass_first", "pass_second", "control", "combine", "setup")

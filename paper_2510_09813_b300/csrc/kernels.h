@@ -76,6 +76,14 @@ constexpr int kDiagStride = 2 * kDiagHalf;
 cudaError_t launch_diag_table(const StepParams* sp, const double* vmat, int n, int L, int64_t num_tiles, void* out,
                               bool c64, cudaStream_t stream);
 
+// Laser phase by the gauge transform U = exp(-i sum_q phi_q n_q) (phase_kernels.cu):
+// a table of exp(i theta) split at bit L, theta(b) = sum_q phi_q b_q, and
+// psi_b *= exp(+i theta(b)) (conj = false: U^dagger) or exp(-i theta(b)) (U).
+size_t phase_table_bytes(int n, int L, bool c64);
+cudaError_t launch_phase_table(const StepParams* sp, int n, int L, void* table, bool c64, cudaStream_t stream);
+cudaError_t launch_phase_apply(void* psi, int n, int L, const void* table, bool conj, bool c64, int grid,
+                               cudaStream_t stream);
+
 // Tensor maps of the strided pass's two input tiles.
 struct TileMaps {
   CUtensorMap x;

@@ -546,6 +546,9 @@ struct rsv_solver {
   double* d_vmat = nullptr;
   void* d_qtab = nullptr;
   void* d_diag = nullptr;    // per-tile diagonal half tables of the current step
+  void* d_phase = nullptr;   // laser-phase gauge tables of the current step (two-pass plans with phi)
+  int phase_bits = 0;        // their split bit L
+  bool phi_now = false;      // the passes of the running step use complex flip coefficients
   void* d_psi = nullptr;
   void* d_u[2] = {nullptr, nullptr};
   std::vector<void*> basis;
@@ -623,6 +626,7 @@ struct rsv_solver {
     d_vmat = nullptr;
     d_qtab = nullptr;
     d_diag = nullptr;
+    d_phase = nullptr;
     d_u[0] = d_u[1] = nullptr;
     basis.clear();
     d_basis = nullptr;
@@ -778,10 +782,10 @@ struct rsv_solver {
     if (!plan.two_pass) {
       if (ctl) a.ctl = *ctl;
       RSV_TRY(launch(RSV_KERNEL_PASS_FIRST, first_bytes,
-                     [&] { return launch_tile(a, nullptr, TileMode::kLanczosSingle, c64, phi, plan.grid_a, stream); }));
+                     [&] { return launch_tile(a, nullptr, TileMode::kLanczosSingle, c64, phi_now, plan.grid_a, stream); }));
     } else {
       RSV_TRY(launch(RSV_KERNEL_PASS_FIRST, first_bytes,
-                     [&] { return launch_tile(a, nullptr, TileMode::kLanczosFirst, c64, phi, plan.grid_a, stream); }));
+                     [&] { return launch_tile(a, nullptr, TileMode::kLanczosFirst, c64, phi_now, plan.grid_a, stream); }));
       TileArgs b = base_args(plan.b, step);
       b.xin = basis[j];
       b.out = u_out;
@@ -789,7 +793,7 @@ struct rsv_solver {
       RSV_TRY(launch(RSV_KERNEL_PASS_SECOND, vec_bytes() * 3,
                      [&] {
                        TileMaps maps{map_basis[j], map_u[j & 1]};
-                       return launch_tile(b, &maps, TileMode::kLanczosSecond, c64, phi, plan.grid_b, stream);
+                       return launch_tile(b, &maps, TileMode::kLanczosSecond, c64, phi_now, plan.grid_b, stream);
                      }));
     }
     return RSV_OK;
@@ -803,6 +807,21 @@ struct rsv_solver {
     RSV_TRY(launch(RSV_KERNEL_SETUP, 0.0, [&] {
       return launch_diag_table(d_sp + k, d_vmat, n, plan.a.L, plan.a.num_tiles, d_diag, c64, stream);
     }));
+    // A step with a laser phase on the two-pass plan runs in the gauge frame:
+    // exp(-i tau H(phi)) = U exp(-i tau H(0)) U^dagger with the diagonal
+    // U = exp(-i sum_q phi_q n_q), so the passes keep real flip coefficients.
+    // Norm and occupations are the same in both frames.
+    const bool gauge = d_phase && step_has_phi(k);
+    phi_now = phi && !gauge;
+    const int phase_grid = ctx->num_sms * 8;
+    if (gauge) {
+      RSV_TRY(launch(RSV_KERNEL_SETUP, 0.0, [&] {
+        return launch_phase_table(d_sp + k, n, phase_bits, d_phase, c64, stream);
+      }));
+      RSV_TRY(launch(RSV_KERNEL_SETUP, 2.0 * vec_bytes(), [&] {
+        return launch_phase_apply(d_psi, n, phase_bits, d_phase, false, c64, phase_grid, stream);
+      }));
+    }
     const int m_max = cfg.m_max;
     int restarts = 0;
     while (true) {
@@ -846,7 +865,19 @@ struct rsv_solver {
       stats.substeps += 1;
       RSV_TRY(begin(0.0, 0, nullptr));
     }
+    if (gauge) {
+      RSV_TRY(launch(RSV_KERNEL_SETUP, 2.0 * vec_bytes(), [&] {
+        return launch_phase_apply(d_psi, n, phase_bits, d_phase, true, c64, phase_grid, stream);
+      }));
+      stats.phase_gauge_steps += 1;
+    }
     return RSV_OK;
+  }
+
+  bool step_has_phi(int k) const {
+    for (int q = 0; q < n; ++q)
+      if (h_sp[k].phi[q] != 0.0) return true;
+    return false;
   }
 
   rsv_status step_once() {
@@ -1471,6 +1502,11 @@ static rsv_status solver_create(rsv_ctx* ctx, const rsv_problem* problem, const 
   A(sizeof(double) * partials_doubles(ctx->num_sms), (void**)&s->d_part);
   A(sizeof(double) * partials_doubles(ctx->num_sms), (void**)&s->d_cpart);
   A(sizeof(double) * n * s->max_rows, (void**)&s->d_occ);
+  if (s->phi && s->plan.two_pass) {
+    // gauge tables (within the footprint's 2 MiB of tables: at most 1 MiB, at 30 atoms complex128)
+    s->phase_bits = (n + 1) / 2;
+    A(phase_table_bytes(n, s->phase_bits, s->c64), &s->d_phase);
+  }
   if (st != RSV_OK) {
     delete s;
     return st;

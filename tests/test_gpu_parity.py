@@ -335,6 +335,34 @@ def test_random_problems_with_phase(ctx, n, prec):
     assert np.max(np.abs(occ - occ_ref)) <= OCC_TOL[prec]
 
 
+@pytest.fixture(scope="module")
+def phase_gauge_ref():
+    n = 21
+    rng = np.random.Generator(np.random.PCG64(700 + n))
+    base = W.random_knot_problem(rng, n, 47, with_phi=True)
+    t = np.arange(47)
+    phi = np.stack([base.phi[0] + rng.uniform(-np.pi, np.pi) + 0.02 * (q + 1) * t for q in range(n)])
+    prob = W.Problem(base.positions, base.c6, 47, base.omega, base.delta, phi)
+    psi0 = W.random_state(700 + n, n)
+    ref, occ_ref = oracle_evolve(prob, 7, psi0=psi0)
+    return prob, psi0, ref, occ_ref
+
+
+@pytest.mark.parametrize("prec", ["c64", "c128"])
+def test_phase_gauge_on_two_pass_plans(ctx, phase_gauge_ref, prec):
+    """A laser phase on the two-pass plans runs in the gauge frame (psi <- U^dagger
+    psi, real-coefficient passes, psi <- U psi, U = exp(-i sum phi_i n_i)): 21
+    atoms, per-atom phases that change every step, a random start state and a
+    ragged last step, against the oracle, with every step counted as gauged."""
+    prob, psi0, ref, occ_ref = phase_gauge_ref
+    psi, occ, st = gpu_evolve(ctx, prob, 7, prec, initial_state=psi0)
+    assert st["tile_passes"] == 2 and st["phase_gauge_steps"] == st["steps"] == 7
+    assert O.infidelity(psi, ref) <= INFID_TOL[prec]
+    if prec == "c128":
+        assert O.norm_difference(psi, ref) <= 1e-9
+    assert np.max(np.abs(occ - occ_ref)) <= OCC_TOL[prec]
+
+
 def test_per_atom_pulses(ctx):
     rng = np.random.Generator(np.random.PCG64(17))
     n, t_ns = 9, 60
