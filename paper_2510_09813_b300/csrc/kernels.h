@@ -136,6 +136,7 @@ struct CombineArgs {
   double* partials;        // [grid][n+1]
   int combine;
   int mask_bit = -1;       // observe only: >= 0 counts only amplitudes whose bit mask_bit is 1
+  int* err = nullptr;      // device error word (bounded waits of the TMA combine); null: per-thread loads
 };
 cudaError_t launch_combine(const CombineArgs& a, bool c64, int grid, cudaStream_t stream);
 

@@ -231,7 +231,194 @@ __global__ void __launch_bounds__(kThreads) combine_kernel(const CombineArgs A) 
   block_reduce_write<kMaxAtoms + 1>(out, s_red, A.partials + (int64_t)blockIdx.x * (n + 1), n + 1);
 }
 
+// ---------------------------------------------------------------------------
+// Combine through a TMA ring: combine_kernel's combine mode on registers of at
+// least one full chunk, with the same arithmetic in the same order (psi summed
+// over the basis in index order, then the observation sums over the thread's
+// vectors). Each basis vector's 64 KiB chunk tile comes into shared memory by
+// one bulk copy, two tiles ahead of the one being summed (128 KiB in flight per
+// SM, where eight 16-byte loads per thread kept 64 KiB).
+// ---------------------------------------------------------------------------
+constexpr int kCombStages = 3;
+
+template <typename Real>
+struct CombTma {
+  static constexpr int V = CplxT<Real>::kLogVec;
+  static constexpr int KK = 4;                   // register bits
+  static constexpr int T = V + 8 + KK;           // chunk bits: vector lane, 8 thread bits, register bits
+  static constexpr int K = 1 << KK;              // vectors per thread
+  static constexpr uint32_t kTileBytes = (1u << T) * 2u * (uint32_t)sizeof(Real);
+};
+static_assert(CombTma<float>::kTileBytes == 65536 && CombTma<double>::kTileBytes == 65536, "64 KiB tiles");
+
+template <typename Real>
+__global__ void __launch_bounds__(kThreads, 1) combine_tma_kernel(const CombineArgs A) {
+  using C = CombTma<Real>;
+  using vec = typename CplxT<Real>::vec;
+  using Acc = typename AccFor<Real>::type;
+  constexpr int V = C::V, NV = 1 << V, R = 2 * NV, T = C::T, K = C::K, KK = C::KK;
+  constexpr uint32_t kTile = C::kTileBytes;
+  extern __shared__ __align__(1024) unsigned char ring[];
+  __shared__ __align__(8) uint64_t full[kCombStages], empty[kCombStages];
+  __shared__ Real s_cr[kMaxKrylov], s_ci[kMaxKrylov];
+  __shared__ const unsigned char* s_basis[kMaxKrylov];
+  __shared__ double s_red[(kMaxAtoms + 1) * (kThreads / 32)];
+  __shared__ double s_hi[kThreads / 32][kMaxAtoms];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int n = A.n;
+  s_hi[warp][lane] = 0.0;
+  const int m = A.ks->m;
+  if (tid < m) {
+    s_cr[tid] = (Real)A.ks->coef_re[tid];
+    s_ci[tid] = (Real)A.ks->coef_im[tid];
+    s_basis[tid] = static_cast<const unsigned char*>(A.basis[tid]);
+  }
+  if (tid == 0) {
+    for (int s = 0; s < kCombStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], kThreads / 32);
+    }
+    mbar_fence_init();
+  }
+  __syncthreads();
+  const int64_t nchunks = A.dim >> T;
+  const int64_t my_chunks =
+      (int64_t)blockIdx.x < nchunks ? (nchunks - 1 - (int64_t)blockIdx.x) / gridDim.x + 1 : 0;
+  const int64_t items = my_chunks * m;  // item q: chunk q / m of this CTA, basis vector q % m
+
+  // ---- producer (warp 0): item q into stage q % kCombStages ----
+  int64_t produced = 0;
+  bool prod_ok = true;
+  auto produce = [&](int64_t q) {
+    if (q >= items || !prod_ok) return;
+    const int s = (int)(q % kCombStages);
+    const int64_t r = q / kCombStages;
+    if (q >= kCombStages) {
+      int okw = 1;
+      if (lane == 0) okw = mbar_wait(&empty[s], (uint32_t)((r - 1) & 1)) ? 1 : 0;
+      okw = __shfl_sync(0xffffffffu, okw, 0);
+      if (!okw) {
+        prod_ok = false;
+        if (lane == 0) atomicOr(A.err, 1);
+        return;
+      }
+    }
+    if (lane == 0) {
+      const int64_t ch = (int64_t)blockIdx.x + (q / m) * gridDim.x;
+      mbar_arrive_expect_tx(&full[s], kTile);
+      tma_load_1d(ring + (size_t)s * kTile, s_basis[q % m] + ch * kTile, kTile, &full[s]);
+    }
+    __syncwarp();
+    produced = q + 1;
+  };
+  if (warp == 0)
+    for (int64_t q = 0; q < kCombStages - 1; ++q) produce(q);
+
+  Acc tot, lane_acc, reg_acc[KK];
+  bool ok = true;
+  int64_t q = 0;
+  for (int64_t i = 0; i < my_chunks && ok; ++i) {
+    const int64_t ch = (int64_t)blockIdx.x + i * gridDim.x;
+    Real x[K][R];
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+#pragma unroll
+      for (int e = 0; e < R; ++e) x[k][e] = 0;
+    for (int j = 0; j < m; ++j, ++q) {
+      if (warp == 0) produce(q + kCombStages - 1);
+      const int s = (int)(q % kCombStages);
+      if (!mbar_wait(&full[s], (uint32_t)((q / kCombStages) & 1))) {
+        if (lane == 0) atomicOr(A.err, 1);
+        ok = false;
+        break;
+      }
+      const vec* tile = reinterpret_cast<const vec*>(ring + (size_t)s * kTile);
+      const Real cr = s_cr[j], ci = s_ci[j];
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        Real b[R];
+        *reinterpret_cast<vec*>(b) = tile[tid | (k << 8)];
+#pragma unroll
+        for (int e = 0; e < NV; ++e) {
+          x[k][2 * e] = fma(cr, b[2 * e], x[k][2 * e]);
+          x[k][2 * e] = fma(-ci, b[2 * e + 1], x[k][2 * e]);
+          x[k][2 * e + 1] = fma(cr, b[2 * e + 1], x[k][2 * e + 1]);
+          x[k][2 * e + 1] = fma(ci, b[2 * e], x[k][2 * e + 1]);
+        }
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[s]);
+    }
+    if (!ok) break;
+    // psi and this chunk's observation sums, vector by vector as combine_kernel
+    Acc ct;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const int64_t vidx = ((ch << T) >> V) + (tid | (k << 8));
+      reinterpret_cast<vec*>(A.psi)[vidx] = *reinterpret_cast<const vec*>(x[k]);
+      Acc pv;
+#pragma unroll
+      for (int e = 0; e < NV; ++e) {
+        Acc pe;
+        pe.dot(x[k][2 * e], x[k][2 * e]);
+        pe.dot(x[k][2 * e + 1], x[k][2 * e + 1]);
+        if (V == 1 && e == 1) lane_acc.merge_acc(pe);
+        pv.merge_acc(pe);
+      }
+      ct.merge_acc(pv);
+#pragma unroll
+      for (int jr = 0; jr < KK; ++jr)
+        if ((k >> jr) & 1) reg_acc[jr].merge_acc(pv);
+    }
+    tot.merge_acc(ct);
+    Acc cw = ct;
+    warp_merge(cw);
+    if (T + lane < n && ((ch >> lane) & 1)) s_hi[warp][lane] += cw.value();
+  }
+  // On an aborted run, let copies still in flight into the ring land (bounded)
+  if (warp == 0 && lane == 0 && !ok)
+    for (int64_t ip = produced - 1; ip >= 0 && ip >= produced - kCombStages; --ip)
+      mbar_wait(&full[ip % kCombStages], (uint32_t)((ip / kCombStages) & 1));
+  __syncthreads();
+  Acc out[kMaxAtoms + 1];
+  out[0] = tot;
+  for (int qb = 0; qb < n; ++qb) {
+    Acc v;
+    if (qb < V) v = lane_acc;
+    else if (qb < V + 8) { if ((tid >> (qb - V)) & 1) v = tot; }
+    else if (qb < T) {
+#pragma unroll
+      for (int jr = 0; jr < KK; ++jr)
+        if (jr == qb - V - 8) v = reg_acc[jr];
+    }
+    else if (lane == 0) {
+      v.add_double(s_hi[warp][qb - T]);
+    }
+    out[1 + qb] = v;
+  }
+  block_reduce_write<kMaxAtoms + 1>(out, s_red, A.partials + (int64_t)blockIdx.x * (n + 1), n + 1);
+}
+
+template <typename Real>
+static cudaError_t launch_combine_tma(const CombineArgs& a, int grid, cudaStream_t stream) {
+  const size_t smem = (size_t)kCombStages * CombTma<Real>::kTileBytes;
+  static bool configured = false;  // per instantiation
+  if (!configured) {
+    const cudaError_t e =
+        cudaFuncSetAttribute(combine_tma_kernel<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  combine_tma_kernel<Real><<<grid, kThreads, smem, stream>>>(a);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_combine(const CombineArgs& a, bool c64, int grid, cudaStream_t stream) {
+  // combine mode on registers of at least one full chunk, with an error word
+  // for the ring's bounded waits: the TMA ring; otherwise per-thread loads
+  const int T = c64 ? CombTma<float>::T : CombTma<double>::T;
+  if (a.combine && a.err && a.n >= T)
+    return c64 ? launch_combine_tma<float>(a, grid, stream) : launch_combine_tma<double>(a, grid, stream);
   if (c64)
     combine_kernel<float><<<grid, kThreads, 0, stream>>>(a);
   else

@@ -728,6 +728,7 @@ struct rsv_solver {
     ca.psi = d_psi;
     ca.partials = d_cpart;
     ca.combine = combine_flag;
+    ca.err = err_ptr(d_ks);
     const double bytes = combine_flag ? vec_bytes() * (m + 1) : vec_bytes();
     return launch(RSV_KERNEL_COMBINE, bytes, [&] { return launch_combine(ca, c64, plan.grid_c, stream); });
   }
