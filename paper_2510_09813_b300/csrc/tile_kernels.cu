@@ -154,6 +154,11 @@ __global__ void __launch_bounds__(kTileThreads, 1)
         tma_load_1d(stage_tile(s, 0), static_cast<const unsigned char*>(args.xin) + off, tile_bytes, &full[s]);
         if (has_prev)
           tma_load_1d(stage_tile(s, 1), static_cast<const unsigned char*>(args.xprev) + off, tile_bytes, &full[s]);
+        else if (tile + 2 * (int64_t)gridDim.x < num_tiles)
+          // one operand per stage leaves half the ring's bytes in flight: keep
+          // the DRAM reads of the tile two beyond this one going through L2
+          prefetch_l2_1d(static_cast<const unsigned char*>(args.xin) + off + 2 * (size_t)gridDim.x * tile_bytes,
+                         tile_bytes);
       } else {
         const int cf1 = (int)f1_of(tile), cf2 = (int)f2_of(tile);
         mbar_arrive_expect_tx(&full[s], tile_bytes * 2);

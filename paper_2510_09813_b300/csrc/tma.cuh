@@ -106,6 +106,11 @@ __device__ __forceinline__ void tma_prefetch_l2_5d(const CUtensorMap* map, int c
                : "memory");
 }
 
+// Contiguous prefetch into L2 (16-byte aligned address, size a multiple of 16).
+__device__ __forceinline__ void prefetch_l2_1d(const void* src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
 // Named barrier over `count` threads (a multiple of 32), id 1..15.
 __device__ __forceinline__ void named_bar_sync(int id, int count) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
